@@ -1,0 +1,220 @@
+/*
+ * mppi_jump.h -- C ABI of libmppi_jump.so: GB300 (sm_103a) MPPI on jump
+ * diffusion processes, after Wang, Williams & Theodorou, "Information
+ * Theoretic Model Predictive Control on Jump Diffusion Processes".
+ *
+ * One optimisation iteration (Algorithm 1) is
+ *   rollout_cost : sample delta ~ N(0, c diag(sigma^2)) per rollout and step,
+ *                  jump counts (compound Poisson, E[dP] = nu dt, Eq. 2, or the
+ *                  zero-one jump timer of Algorithm 1) and marks, roll the
+ *                  plant out with Euler steps and accumulate the augmented
+ *                  cost S~ of Eq. 34-35;
+ *   update       : weights w_k = exp(-S~_k/lambda) / sum exp(-S~/lambda)
+ *                  (Eq. 36-37) and U_j += alpha sum_k w_k delta_eff_{k,j}
+ *                  (Eq. 37 with alpha of Eq. 49);
+ *   step         : `iters` iterations from the same x0, then execute u_0,
+ *                  shift and append u_init (Algorithm 1, MPC loop of Sec. V).
+ *
+ * Conventions for every call below.
+ *   - Pointers are DEVICE pointers unless the argument name ends in `_host`.
+ *   - Device work is enqueued on the context's stream (given at init); calls
+ *     return once the work is enqueued, except those with host outputs, which
+ *     synchronise that stream before returning.
+ *   - Errors are returned as mppi_status codes; nothing aborts, traps or
+ *     throws.  mppi_jump_last_error() gives a message for the last failure on
+ *     a context.  Device-side conditions (all costs non-finite) are recorded
+ *     in a status word that the next synchronising call returns.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - All arrays are dense, row-major, float32 unless stated:
+ *       x0 [n], U [T][m], costs [K], weights [K],
+ *       noise delta_eff [T][K][m] (step-major: all rollouts of step 0 first),
+ *       counts [T][K] uint8, jumps J [T][K][q].
+ *     n = 4, m = 1 for the cart-pole; n = 12, m = 4 for the quadrotor.
+ */
+#ifndef MPPI_JUMP_H
+#define MPPI_JUMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPPI_JUMP_ABI_VERSION 1
+#define MPPI_MAX_JUMPS 16 /* largest jump count per step the sampler draws */
+
+typedef enum {
+  MPPI_OK = 0,
+  MPPI_EINVAL = 1,     /* invalid argument or configuration */
+  MPPI_ENOMEM = 2,     /* device or host allocation failed, or over budget */
+  MPPI_ECUDA = 3,      /* a CUDA runtime call failed */
+  MPPI_ETIMEOUT = 4,   /* a bounded device wait gave up */
+  MPPI_ENONFINITE = 5, /* every rollout cost was non-finite: U left unchanged */
+  MPPI_EBUSY = 6       /* resource in use (e.g. session already has a request) */
+} mppi_status;
+
+typedef enum { MPPI_CARTPOLE = 0, MPPI_QUADROTOR = 1 } mppi_system;
+typedef enum { MPPI_COUNT_POISSON = 0, MPPI_COUNT_BERNOULLI = 1 } mppi_count_law;
+typedef enum { MPPI_MARK_NORMAL = 0, MPPI_MARK_LAPLACE = 1 } mppi_mark_law;
+typedef enum { MPPI_JUMP_STATE = 0, MPPI_JUMP_CONTROL = 1 } mppi_jump_channel;
+typedef enum { MPPI_NOISE_F32 = 0, MPPI_NOISE_BF16 = 1 } mppi_noise_dtype;
+
+/* Plant constants.  Cart-pole: point-mass pole, theta = 0 hanging down,
+ * q(x) = (x-goal)^T diag(Q) (x-goal), phi(x) = (x-goal)^T diag(Qf) (x-goal).
+ * Quadrotor: state (p, v, eta = ZYX Euler angles, omega = body rates), rotor
+ * thrusts in a "+" layout (1,2,3,4 on +x,+y,-x,-y), torque
+ * (arm (f2-f4), arm (f3-f1), kappa (f1-f2+f3-f4));
+ * q(x) = wp|p-goal|^2 + wv|v|^2 + weta|eta|^2 + wom|omega|^2
+ *        + obs_cost [|p-obs|^2 < obs_r^2],  phi(x) = q(x) without the indicator. */
+typedef struct {
+  float mc, mp, l, g;
+  float goal[4], Q[4], Qf[4];
+} mppi_cartpole_params;
+
+typedef struct {
+  float mass, J[3], arm, kappa, g;
+  float goal[3], wp, wv, weta, wom;
+  float obs[3], obs_r, obs_cost;
+} mppi_quadrotor_params;
+
+/* Problem configuration: the "Given" list of Algorithm 1 (M = K samples,
+ * N = T steps, dt, plant f/G/B/H, cost phi/q/lambda/R, noise c/Sigma_D/
+ * Sigma_J/nu, u_init).  R is implied by Eq. 14 (R = lambda G^T Sigma^-1 G) and
+ * B = G (Sec. IV), so the control cost follows from sigma and lambda. */
+typedef struct {
+  int32_t system;        /* mppi_system */
+  int32_t K;             /* rollouts, 1 .. 2^24 */
+  int32_t T;             /* horizon steps, 1 .. 4096 */
+  float dt;              /* step, > 0 */
+  float lambda;          /* temperature, > 0 */
+  float c;               /* exploration variance scale of Eq. 33, > 0 */
+  float alpha;           /* step size of Eq. 49 (1 gives Eq. 36) */
+  float sigma[4];        /* std of the control perturbation delta = eps/sqrt(dt) */
+  float jump_rate;       /* nu, jumps per second, >= 0 */
+  int32_t count_law;     /* mppi_count_law */
+  int32_t mark_law;      /* mppi_mark_law */
+  float mark_scale[4];   /* Normal std / Laplace scale per mark component */
+  int32_t jump_channel;  /* mppi_jump_channel */
+  int32_t q;             /* mark dimension (must equal m for MPPI_JUMP_CONTROL) */
+  int32_t jump_rows[4];  /* state rows hit by the marks (MPPI_JUMP_STATE) */
+  int32_t jump_sqrt_dt;  /* state mode: 1 scales the jump by sqrt(dt) */
+  int32_t noise_dtype;   /* mppi_noise_dtype for the stored delta_eff */
+  float u_init[4];       /* appended after each MPC shift */
+  uint64_t seed;         /* Philox key: (seed mod 2^32, seed >> 32) */
+  mppi_cartpole_params cartpole;
+  mppi_quadrotor_params quadrotor;
+  int32_t reserved;      /* must be 0 */
+} mppi_jump_config;
+
+typedef struct mppi_jump_ctx mppi_jump_ctx;
+
+/* Fills *out with the defaults for `system` (the cart-pole swing-up or the
+ * quadrotor waypoint flight, K = 1000 / 4096 rollouts).  Host only. */
+mppi_status mppi_jump_default_config(int32_t system, mppi_jump_config* out);
+
+/* Checks a configuration without touching the GPU. */
+mppi_status mppi_jump_validate(const mppi_jump_config* cfg);
+
+/* sizeof(mppi_jump_config) as compiled into the library, so that bindings
+ * can verify their struct layout. */
+size_t mppi_jump_config_bytes(void);
+
+/* Jump-count threshold table for rate nu and step dt (host only).  Poisson:
+ * thr[n-1] = ceil(2^32 F(n-1; nu dt)), F the Poisson CDF summed term by term
+ * (term_0 = e^-mu, term_n = term_{n-1} mu / n), a word w giving the count
+ * #{n : w >= thr[n-1]}; entries that would equal 2^32 end the table (*nmax).
+ * Bernoulli: thr[0] = round(2^32 nu dt), count = [w < thr[0]].  Returns
+ * MPPI_EINVAL when nu dt is negative or non-finite, when the Poisson tail
+ * beyond MPPI_MAX_JUMPS is not negligible (> 2^-32), or Bernoulli nu dt >= 1. */
+mppi_status mppi_jump_count_table(float jump_rate, float dt, int32_t count_law,
+                                  uint32_t thr_host[MPPI_MAX_JUMPS], int32_t* nmax_host);
+
+/* Device bytes a context with this configuration allocates. */
+mppi_status mppi_jump_workspace_bytes(const mppi_jump_config* cfg, size_t* bytes_host);
+
+/* Creates a context on the current device: allocates the perturbation,
+ * cost, weight and control buffers (cudaMalloc), sets U = u_init for every
+ * step and the iteration counter to 0.  `stream` is the cudaStream_t on which
+ * every later call enqueues its work; NULL makes the context create and own a
+ * non-blocking stream (the caller then orders its own work with
+ * mppi_jump_sync).  Fails with MPPI_ENOMEM when the device allocation fails.
+ * The context owns its device memory until mppi_jump_destroy. */
+mppi_status mppi_jump_init(const mppi_jump_config* cfg, void* stream, mppi_jump_ctx** out);
+
+/* Frees everything the context owns (synchronises its stream).  NULL is a no-op. */
+mppi_status mppi_jump_destroy(mppi_jump_ctx* ctx);
+
+/* Message describing the last failure on ctx (static string when ctx is NULL). */
+const char* mppi_jump_last_error(const mppi_jump_ctx* ctx);
+const char* mppi_jump_status_string(mppi_status st);
+
+/* Replaces / reads the control sequence U [T][m] (device pointers). */
+mppi_status mppi_jump_set_controls(mppi_jump_ctx* ctx, const float* U);
+mppi_status mppi_jump_get_controls(mppi_jump_ctx* ctx, float* U);
+
+/* Sets / reads the iteration counter that selects the Philox stream. */
+mppi_status mppi_jump_set_iteration(mppi_jump_ctx* ctx, uint32_t it);
+mppi_status mppi_jump_get_iteration(mppi_jump_ctx* ctx, uint32_t* it_host);
+
+/* A1+A2 (Algorithm 1 sampling and rollout loop; Eq. 2, 4, 34-35): for the
+ * current iteration counter, samples the noise, rolls out all K rollouts
+ * from x0 [n] under the context's U and stores delta_eff and the costs in
+ * the context.  If `costs` is not NULL it receives S~ [K]. */
+mppi_status mppi_jump_rollout_cost(mppi_jump_ctx* ctx, const float* x0, float* costs);
+
+/* A3+A4 (Eq. 36-37, 49): softmin weights of the last rollout_cost and the
+ * in-place update of the context's U, then counter += 1.  If every cost was
+ * non-finite, U is left unchanged and the next synchronising call returns
+ * MPPI_ENONFINITE. */
+mppi_status mppi_jump_update(mppi_jump_ctx* ctx);
+
+/* A5 (Algorithm 1 MPC loop): `iters` x (rollout_cost + update) from the same
+ * x0, then u0 = U_0, U_i <- U_{i+1}, U_{T-1} <- u_init.  The work is replayed
+ * from a CUDA graph captured on first use for each `iters`.
+ * mppi_jump_step takes HOST x0 [n] and writes HOST u0 [m] (synchronous);
+ * mppi_jump_step_async takes device pointers and does not synchronise. */
+mppi_status mppi_jump_step(mppi_jump_ctx* ctx, const float* x0_host, int32_t iters,
+                           float* u0_host);
+mppi_status mppi_jump_step_async(mppi_jump_ctx* ctx, const float* x0, int32_t iters,
+                                 float* u0);
+
+/* Phase timing.  With timing enabled, each MPC step records CUDA events
+ * around every rollout launch and every weights+update launch (event record
+ * nodes inside the replayed graph); mppi_jump_phase_times synchronises and
+ * returns the summed durations of the last step in milliseconds
+ * (out_host[0] = rollout, out_host[1] = softmin + update) and the number
+ * of iterations they cover in *iters_host.  Enabling or disabling timing
+ * drops the cached graphs. */
+mppi_status mppi_jump_enable_timing(mppi_jump_ctx* ctx, int32_t on);
+mppi_status mppi_jump_phase_times(mppi_jump_ctx* ctx, float out_host[2], int32_t* iters_host);
+
+/* Synchronises the context's stream and returns (then clears) the device
+ * status word: MPPI_OK or MPPI_ENONFINITE. */
+mppi_status mppi_jump_sync(mppi_jump_ctx* ctx);
+
+/* Debug outputs of the following rollout_cost calls (NULL disables):
+ * counts [T][K] uint8 jump counts, jumps [T][K][q] summed marks J. */
+mppi_status mppi_jump_set_debug(mppi_jump_ctx* ctx, uint8_t* counts, float* jumps);
+
+/* Copies of the last iteration's intermediates:
+ * noise: delta_eff [T][K][m] in the context's noise dtype (float32 or
+ * bfloat16 bits); weights: w [K]; free energy (host, 3 floats):
+ * rho = min S~, Z = sum exp(-(S~-rho)/lambda), F = rho/lambda - ln(Z/K)
+ * (the Monte Carlo form of Eq. 5).  The free-energy call synchronises. */
+mppi_status mppi_jump_get_noise(mppi_jump_ctx* ctx, void* noise);
+mppi_status mppi_jump_get_weights(mppi_jump_ctx* ctx, float* weights);
+mppi_status mppi_jump_get_free_energy(mppi_jump_ctx* ctx, float out_host[3]);
+
+/* Checkpoint: serialises (configuration, U, counter) into buf_host.  With
+ * buf_host NULL, *size_host receives the size needed.  Restoring into a
+ * context created from the same configuration continues the random stream
+ * exactly, so restore-then-solve equals solve-without-interruption. */
+mppi_status mppi_jump_get_state(mppi_jump_ctx* ctx, void* buf_host, size_t* size_host);
+mppi_status mppi_jump_set_state(mppi_jump_ctx* ctx, const void* buf_host, size_t size);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPPI_JUMP_H */

@@ -1,0 +1,230 @@
+// device.cuh -- device-side building blocks of the MPPI jump-diffusion path:
+// the Philox4x32-10 counter generator, uniforms and Box-Muller normals, the
+// jump sampler, the two plants and their costs, and compensated summation.
+// Everything here runs in registers inside the fused kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mj {
+
+constexpr int kMaxJumps = 16;
+
+// Plant constants, pre-processed on the host (reciprocals, squared radius).
+struct DevPlant {
+  // cart-pole: point-mass pole, theta = 0 hanging down
+  float mc, mp, l, g, inv_l, mcp_g;  // mcp_g = (mc + mp) g
+  float goal[4], Q[4], Qf[4];
+  // quadrotor
+  float inv_mass, J[3], invJ[3], arm, kappa, qg;
+  float pgoal[3], wp, wv, weta, wom, obs[3], obs_r2, obs_cost;
+};
+
+// Everything a rollout needs, passed by value as a kernel parameter.
+struct DevProblem {
+  int32_t system, K, Kpad, T, n, m, q;
+  int32_t count_law, mark_law, jump_channel, nmax, noise_bf16;
+  int32_t jump_rows[4];
+  uint32_t key0, key1;
+  uint32_t thr[kMaxJumps];  // jump-count thresholds (see the header)
+  float dt, lam, inv_lam, is_coef, alpha, s_jump;
+  float sqc_sigma[4];   // sqrt(c) * sigma_i
+  float inv_sigma2[4];  // 1 / sigma_i^2
+  float mark_scale[4];
+  float u_init[4];
+  DevPlant pl;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds, each two
+// 32x32->64-bit products whose high halves are xored with the other two
+// counter words and the round key; the key advances by the Weyl constants
+// (golden ratio, sqrt(3) - 1) between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// Uniform on (0, 1): (top 23 bits + 1/2) * 2^-23, exact in float32.
+__device__ __forceinline__ float uniform01(uint32_t w) {
+  return (__uint2float_rn(w >> 9) + 0.5f) * 0x1p-23f;
+}
+
+// Box-Muller (1958): r = sqrt(-2 ln u_a), (r cos 2 pi u_b, r sin 2 pi u_b).
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, float& z1) {
+  const float r = sqrtf(-2.0f * logf(uniform01(wa)));
+  float s, c;
+  sincospif(2.0f * uniform01(wb), &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+__device__ __forceinline__ void normals4(const uint4 w, float z[4]) {
+  box_muller(w.x, w.y, z[0], z[1]);
+  box_muller(w.z, w.w, z[2], z[3]);
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 w, int i) {
+  return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w));
+}
+
+// Jump count of one step from its 32-bit word (Poisson thresholds or the
+// Bernoulli timer of the zero-one law).
+__device__ __forceinline__ int jump_count(const DevProblem& P, uint32_t w) {
+  if (P.count_law == 1) return (P.nmax > 0 && w < P.thr[0]) ? 1 : 0;
+  int n = 0;
+  while (n < P.nmax && w >= P.thr[n]) ++n;
+  return n;
+}
+
+// Laplace(0, b) mark from a uniform: -b sgn(u - 1/2) ln(1 - 2|u - 1/2|).
+// u - 1/2 and 1 - 2|u - 1/2| are exact for the 23-bit uniforms above.
+__device__ __forceinline__ float laplace_mark(float b, uint32_t w) {
+  const float h = uniform01(w) - 0.5f;
+  const float mag = -b * logf(1.0f - 2.0f * fabsf(h));
+  return h > 0.0f ? mag : -mag;
+}
+
+// ---------------------------------------------------------------------------
+// Compensated summation (Knuth's branch-free TwoSum): (s, c) holds the sum and
+// the accumulated rounding error.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float y) {
+  const float t = __fadd_rn(s, y);
+  const float bp = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(y, bp));
+  c = __fadd_rn(c, e);
+  s = t;
+}
+
+// Merge two compensated pairs.
+__device__ __forceinline__ void two_sum_merge(float& s, float& c, float s2, float c2) {
+  two_sum_acc(s, c, s2);
+  c = __fadd_rn(c, c2);
+}
+
+// ---------------------------------------------------------------------------
+// Plants: F(x, v) = f(x) + G(x) v (Eq. 4), Euler-stepped by the caller.
+// ---------------------------------------------------------------------------
+template <int SYS>
+struct Plant;
+
+// Cart-pole (Lagrangian of a cart with a point-mass pole):
+//   xdd  = [f + mp s (l thd^2 + g c)] / D,            D = mc + mp s^2
+//   thdd = [-f c - mp l thd^2 c s - (mc + mp) g s] / (l D)
+template <>
+struct Plant<0> {
+  static constexpr int n = 4, m = 1;
+  __device__ __forceinline__ static void xdot(const DevPlant& p, const float* x, const float* v,
+                                              float* xd) {
+    float s, c;
+    sincosf(x[2], &s, &c);
+    const float thd = x[3];
+    const float D = p.mc + p.mp * s * s;
+    const float thd2 = thd * thd;
+    const float f = v[0];
+    const float xdd = (f + p.mp * s * (p.l * thd2 + p.g * c)) / D;
+    const float thdd = (-f * c - p.mp * p.l * thd2 * c * s - p.mcp_g * s) / (p.l * D);
+    xd[0] = x[1];
+    xd[1] = xdd;
+    xd[2] = thd;
+    xd[3] = thdd;
+  }
+  __device__ __forceinline__ static float state_cost(const DevPlant& p, const float* x) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float e = x[i] - p.goal[i];
+      s += p.Q[i] * e * e;
+    }
+    return s;
+  }
+  __device__ __forceinline__ static float terminal_cost(const DevPlant& p, const float* x) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float e = x[i] - p.goal[i];
+      s += p.Qf[i] * e * e;
+    }
+    return s;
+  }
+};
+
+// Quadrotor rigid body, ZYX Euler angles, "+" rotor layout:
+//   p' = v,  v' = (sum f / m) R(eta) e3 - g e3,  eta' = W(eta) omega,
+//   J omega' = tau - omega x J omega,
+//   tau = (L (f2 - f4), L (f3 - f1), kappa (f1 - f2 + f3 - f4)).
+template <>
+struct Plant<1> {
+  static constexpr int n = 12, m = 4;
+  __device__ __forceinline__ static void xdot(const DevPlant& p, const float* x, const float* v,
+                                              float* xd) {
+    float sph, cph, sth, cth, sps, cps;
+    sincosf(x[6], &sph, &cph);
+    sincosf(x[7], &sth, &cth);
+    sincosf(x[8], &sps, &cps);
+    const float wp = x[9], wq = x[10], wr = x[11];
+    const float a = (v[0] + v[1] + v[2] + v[3]) * p.inv_mass;
+    xd[0] = x[3];
+    xd[1] = x[4];
+    xd[2] = x[5];
+    xd[3] = a * (cph * sth * cps + sph * sps);
+    xd[4] = a * (cph * sth * sps - sph * cps);
+    xd[5] = a * (cph * cth) - p.qg;
+    const float inv_cth = 1.0f / cth;
+    const float tth = sth * inv_cth;
+    xd[6] = wp + sph * tth * wq + cph * tth * wr;
+    xd[7] = cph * wq - sph * wr;
+    xd[8] = (sph * wq + cph * wr) * inv_cth;
+    const float taux = p.arm * (v[1] - v[3]);
+    const float tauy = p.arm * (v[2] - v[0]);
+    const float tauz = p.kappa * (v[0] - v[1] + v[2] - v[3]);
+    const float Jp = p.J[0] * wp, Jq = p.J[1] * wq, Jr = p.J[2] * wr;
+    xd[9] = (taux - (wq * Jr - wr * Jq)) * p.invJ[0];
+    xd[10] = (tauy - (wr * Jp - wp * Jr)) * p.invJ[1];
+    xd[11] = (tauz - (wp * Jq - wq * Jp)) * p.invJ[2];
+  }
+  __device__ __forceinline__ static float quad_terms(const DevPlant& p, const float* x) {
+    float ep = 0.0f, ev = 0.0f, ee = 0.0f, ew = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float d = x[i] - p.pgoal[i];
+      ep += d * d;
+      ev += x[3 + i] * x[3 + i];
+      ee += x[6 + i] * x[6 + i];
+      ew += x[9 + i] * x[9 + i];
+    }
+    return p.wp * ep + p.wv * ev + p.weta * ee + p.wom * ew;
+  }
+  __device__ __forceinline__ static float state_cost(const DevPlant& p, const float* x) {
+    float eo = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float o = x[i] - p.obs[i];
+      eo += o * o;
+    }
+    const float s = quad_terms(p, x);
+    return eo < p.obs_r2 ? s + p.obs_cost : s;
+  }
+  __device__ __forceinline__ static float terminal_cost(const DevPlant& p, const float* x) {
+    return quad_terms(p, x);
+  }
+};
+
+}  // namespace mj

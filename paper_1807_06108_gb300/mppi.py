@@ -1,0 +1,432 @@
+"""ctypes binding of libmppi_jump.so (argument marshalling only).
+
+Every function named ``mppi_jump_*`` here is the C entry point of the same
+name from ``include/mppi_jump.h``: device buffers are passed as integer
+device pointers (``tensor.data_ptr()``), streams as ``cudaStream_t`` integers
+(``torch.cuda.Stream().cuda_stream``).  Nonzero status codes raise
+:class:`MppiError`.  All compute runs in the library's CUDA kernels; there is
+no CPU or PyTorch fallback: importing this module raises if the library has
+not been built.
+
+:class:`Solver` is a small convenience wrapper that owns a context and the
+PyTorch tensors used to exchange data with it.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+from . import workloads as _wl
+
+LIB_PATH = _build.LIB
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+MAX_JUMPS = 16
+STATUS = {0: "MPPI_OK", 1: "MPPI_EINVAL", 2: "MPPI_ENOMEM", 3: "MPPI_ECUDA",
+          4: "MPPI_ETIMEOUT", 5: "MPPI_ENONFINITE", 6: "MPPI_EBUSY"}
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EBUSY = range(7)
+
+
+class MppiError(RuntimeError):
+    def __init__(self, code, what, detail=""):
+        msg = f"{what}: {STATUS.get(code, code)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+        self.code = code
+
+
+class CartpoleParams(ctypes.Structure):
+    _fields_ = [("mc", ctypes.c_float), ("mp", ctypes.c_float), ("l", ctypes.c_float),
+                ("g", ctypes.c_float), ("goal", ctypes.c_float * 4), ("Q", ctypes.c_float * 4),
+                ("Qf", ctypes.c_float * 4)]
+
+
+class QuadrotorParams(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_float), ("J", ctypes.c_float * 3), ("arm", ctypes.c_float),
+                ("kappa", ctypes.c_float), ("g", ctypes.c_float), ("goal", ctypes.c_float * 3),
+                ("wp", ctypes.c_float), ("wv", ctypes.c_float), ("weta", ctypes.c_float),
+                ("wom", ctypes.c_float), ("obs", ctypes.c_float * 3), ("obs_r", ctypes.c_float),
+                ("obs_cost", ctypes.c_float)]
+
+
+class Config(ctypes.Structure):
+    """mppi_jump_config."""
+    _fields_ = [
+        ("system", ctypes.c_int32), ("K", ctypes.c_int32), ("T", ctypes.c_int32),
+        ("dt", ctypes.c_float), ("lam", ctypes.c_float), ("c", ctypes.c_float),
+        ("alpha", ctypes.c_float), ("sigma", ctypes.c_float * 4),
+        ("jump_rate", ctypes.c_float), ("count_law", ctypes.c_int32),
+        ("mark_law", ctypes.c_int32), ("mark_scale", ctypes.c_float * 4),
+        ("jump_channel", ctypes.c_int32), ("q", ctypes.c_int32),
+        ("jump_rows", ctypes.c_int32 * 4), ("jump_sqrt_dt", ctypes.c_int32),
+        ("noise_dtype", ctypes.c_int32), ("u_init", ctypes.c_float * 4),
+        ("seed", ctypes.c_uint64), ("cartpole", CartpoleParams),
+        ("quadrotor", QuadrotorParams), ("reserved", ctypes.c_int32),
+    ]
+
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_st = ctypes.c_int
+
+
+def _sig(name, restype, *argtypes):
+    f = getattr(_lib, name)
+    f.restype = restype
+    f.argtypes = list(argtypes)
+    return f
+
+
+_CTX = _vp
+_sig("mppi_jump_config_bytes", ctypes.c_size_t)
+if _lib.mppi_jump_config_bytes() != ctypes.sizeof(Config):
+    raise ImportError("mppi_jump_config layout mismatch between the library and this binding")
+_sig("mppi_jump_default_config", _st, ctypes.c_int32, _P(Config))
+_sig("mppi_jump_validate", _st, _P(Config))
+_sig("mppi_jump_count_table", _st, ctypes.c_float, ctypes.c_float, ctypes.c_int32,
+     _P(ctypes.c_uint32), _P(ctypes.c_int32))
+_sig("mppi_jump_workspace_bytes", _st, _P(Config), _P(ctypes.c_size_t))
+_sig("mppi_jump_init", _st, _P(Config), _vp, _P(_vp))
+_sig("mppi_jump_destroy", _st, _CTX)
+_sig("mppi_jump_last_error", ctypes.c_char_p, _CTX)
+_sig("mppi_jump_status_string", ctypes.c_char_p, ctypes.c_int)
+_sig("mppi_jump_set_controls", _st, _CTX, _vp)
+_sig("mppi_jump_get_controls", _st, _CTX, _vp)
+_sig("mppi_jump_set_iteration", _st, _CTX, ctypes.c_uint32)
+_sig("mppi_jump_get_iteration", _st, _CTX, _P(ctypes.c_uint32))
+_sig("mppi_jump_rollout_cost", _st, _CTX, _vp, _vp)
+_sig("mppi_jump_update", _st, _CTX)
+_sig("mppi_jump_step", _st, _CTX, _P(ctypes.c_float), ctypes.c_int32, _P(ctypes.c_float))
+_sig("mppi_jump_step_async", _st, _CTX, _vp, ctypes.c_int32, _vp)
+_sig("mppi_jump_sync", _st, _CTX)
+_sig("mppi_jump_enable_timing", _st, _CTX, ctypes.c_int32)
+_sig("mppi_jump_phase_times", _st, _CTX, _P(ctypes.c_float), _P(ctypes.c_int32))
+_sig("mppi_jump_set_debug", _st, _CTX, _vp, _vp)
+_sig("mppi_jump_get_noise", _st, _CTX, _vp)
+_sig("mppi_jump_get_weights", _st, _CTX, _vp)
+_sig("mppi_jump_get_free_energy", _st, _CTX, _P(ctypes.c_float))
+_sig("mppi_jump_get_state", _st, _CTX, _vp, _P(ctypes.c_size_t))
+_sig("mppi_jump_set_state", _st, _CTX, _vp, ctypes.c_size_t)
+
+
+def _check(st, what, ctx=None):
+    if st != OK:
+        detail = ""
+        if ctx:
+            detail = (_lib.mppi_jump_last_error(ctx) or b"").decode(errors="replace")
+        raise MppiError(st, what, detail)
+
+
+# --------------------------------------------------------------------------
+# Thin wrappers with the C names
+# --------------------------------------------------------------------------
+
+def mppi_jump_default_config(system):
+    cfg = Config()
+    _check(_lib.mppi_jump_default_config(int(system), ctypes.byref(cfg)), "default_config")
+    return cfg
+
+
+def mppi_jump_validate(cfg):
+    return _lib.mppi_jump_validate(ctypes.byref(cfg))
+
+
+def mppi_jump_count_table(jump_rate, dt, count_law=0):
+    thr = (ctypes.c_uint32 * MAX_JUMPS)()
+    nmax = ctypes.c_int32(0)
+    _check(_lib.mppi_jump_count_table(float(jump_rate), float(dt), int(count_law), thr,
+                                      ctypes.byref(nmax)), "count_table")
+    return np.array(list(thr), dtype=np.uint32), nmax.value
+
+
+def mppi_jump_workspace_bytes(cfg):
+    n = ctypes.c_size_t(0)
+    _check(_lib.mppi_jump_workspace_bytes(ctypes.byref(cfg), ctypes.byref(n)), "workspace_bytes")
+    return n.value
+
+
+def mppi_jump_init(cfg, stream=0):
+    ctx = _vp()
+    st = _lib.mppi_jump_init(ctypes.byref(cfg), _vp(stream or None), ctypes.byref(ctx))
+    _check(st, "init")
+    return ctx
+
+
+def mppi_jump_destroy(ctx):
+    _check(_lib.mppi_jump_destroy(ctx), "destroy")
+
+
+def mppi_jump_last_error(ctx):
+    return (_lib.mppi_jump_last_error(ctx) or b"").decode(errors="replace")
+
+
+def mppi_jump_set_controls(ctx, U_ptr):
+    _check(_lib.mppi_jump_set_controls(ctx, _vp(U_ptr)), "set_controls", ctx)
+
+
+def mppi_jump_get_controls(ctx, U_ptr):
+    _check(_lib.mppi_jump_get_controls(ctx, _vp(U_ptr)), "get_controls", ctx)
+
+
+def mppi_jump_set_iteration(ctx, it):
+    _check(_lib.mppi_jump_set_iteration(ctx, int(it) & 0xFFFFFFFF), "set_iteration", ctx)
+
+
+def mppi_jump_get_iteration(ctx):
+    v = ctypes.c_uint32(0)
+    _check(_lib.mppi_jump_get_iteration(ctx, ctypes.byref(v)), "get_iteration", ctx)
+    return v.value
+
+
+def mppi_jump_rollout_cost(ctx, x0_ptr, costs_ptr=0):
+    _check(_lib.mppi_jump_rollout_cost(ctx, _vp(x0_ptr), _vp(costs_ptr or None)),
+           "rollout_cost", ctx)
+
+
+def mppi_jump_update(ctx):
+    _check(_lib.mppi_jump_update(ctx), "update", ctx)
+
+
+def mppi_jump_step(ctx, x0_host, iters, u0_host):
+    """x0_host / u0_host: contiguous float32 numpy arrays (host memory)."""
+    st = _lib.mppi_jump_step(ctx, x0_host.ctypes.data_as(_P(ctypes.c_float)), int(iters),
+                             u0_host.ctypes.data_as(_P(ctypes.c_float)))
+    _check(st, "step", ctx)
+
+
+def mppi_jump_step_async(ctx, x0_ptr, iters, u0_ptr=0):
+    _check(_lib.mppi_jump_step_async(ctx, _vp(x0_ptr), int(iters), _vp(u0_ptr or None)),
+           "step_async", ctx)
+
+
+def mppi_jump_sync(ctx):
+    _check(_lib.mppi_jump_sync(ctx), "sync", ctx)
+
+
+def mppi_jump_enable_timing(ctx, on=True):
+    _check(_lib.mppi_jump_enable_timing(ctx, int(bool(on))), "enable_timing", ctx)
+
+
+def mppi_jump_phase_times(ctx):
+    """(rollout_ms, update_ms, iterations) summed over the last MPC step."""
+    out = (ctypes.c_float * 2)()
+    it = ctypes.c_int32(0)
+    _check(_lib.mppi_jump_phase_times(ctx, out, ctypes.byref(it)), "phase_times", ctx)
+    return float(out[0]), float(out[1]), it.value
+
+
+def mppi_jump_set_debug(ctx, counts_ptr=0, jumps_ptr=0):
+    _check(_lib.mppi_jump_set_debug(ctx, _vp(counts_ptr or None), _vp(jumps_ptr or None)),
+           "set_debug", ctx)
+
+
+def mppi_jump_get_noise(ctx, noise_ptr):
+    _check(_lib.mppi_jump_get_noise(ctx, _vp(noise_ptr)), "get_noise", ctx)
+
+
+def mppi_jump_get_weights(ctx, w_ptr):
+    _check(_lib.mppi_jump_get_weights(ctx, _vp(w_ptr)), "get_weights", ctx)
+
+
+def mppi_jump_get_free_energy(ctx):
+    out = (ctypes.c_float * 3)()
+    _check(_lib.mppi_jump_get_free_energy(ctx, out), "get_free_energy", ctx)
+    return np.array(list(out), dtype=np.float32)
+
+
+def mppi_jump_get_state(ctx):
+    n = ctypes.c_size_t(0)
+    _check(_lib.mppi_jump_get_state(ctx, None, ctypes.byref(n)), "get_state", ctx)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(_lib.mppi_jump_get_state(ctx, buf, ctypes.byref(n)), "get_state", ctx)
+    return bytes(buf.raw[:n.value])
+
+
+def mppi_jump_set_state(ctx, blob):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(_lib.mppi_jump_set_state(ctx, buf, len(blob)), "set_state", ctx)
+
+
+# --------------------------------------------------------------------------
+# Problem dictionaries -> configuration
+# --------------------------------------------------------------------------
+
+def config_from_problem(prob):
+    """mppi_jump_config from a workloads.problem() dictionary."""
+    cfg = Config()
+    cfg.system = 0 if prob["system"] == "cartpole" else 1
+    cfg.K, cfg.T = prob["K"], prob["T"]
+    cfg.dt, cfg.lam, cfg.c, cfg.alpha = prob["dt"], prob["lam"], prob["c"], prob["alpha"]
+    for i, s in enumerate(prob["sigma"]):
+        cfg.sigma[i] = s
+    cfg.jump_rate = prob["nu"]
+    cfg.count_law = {"poisson": 0, "bernoulli": 1}[prob["count_law"]]
+    cfg.mark_law = {"normal": 0, "laplace": 1}[prob["mark_law"]]
+    for i, s in enumerate(prob["mark_scale"]):
+        cfg.mark_scale[i] = s
+    cfg.jump_channel = {"state": 0, "control": 1}[prob["jump_channel"]]
+    cfg.q = prob["q"]
+    for i, r in enumerate(prob["jump_rows"]):
+        cfg.jump_rows[i] = r
+    cfg.jump_sqrt_dt = int(prob["jump_sqrt_dt"])
+    cfg.noise_dtype = {"f32": 0, "bf16": 1}[prob["noise_dtype"]]
+    for i, u in enumerate(prob["u_init"]):
+        cfg.u_init[i] = u
+    cfg.seed = prob["seed"]
+    p = prob["params"]
+    if prob["system"] == "cartpole":
+        c = cfg.cartpole
+        c.mc, c.mp, c.l, c.g = p["mc"], p["mp"], p["l"], p["g"]
+        for i in range(4):
+            c.goal[i], c.Q[i], c.Qf[i] = p["goal"][i], p["Q"][i], p["Qf"][i]
+    else:
+        q = cfg.quadrotor
+        q.mass, q.arm, q.kappa, q.g = p["mass"], p["arm"], p["kappa"], p["g"]
+        for i in range(3):
+            q.J[i], q.goal[i], q.obs[i] = p["J"][i], p["goal"][i], p["obs"][i]
+        q.wp, q.wv, q.weta, q.wom = p["wp"], p["wv"], p["weta"], p["wom"]
+        q.obs_r, q.obs_cost = p["obs_r"], p["obs_cost"]
+    return cfg
+
+
+class Solver:
+    """One MPPI context plus the torch tensors used to talk to it.
+
+    All device work runs on ``self.stream`` (a torch.cuda.Stream).
+    """
+
+    def __init__(self, prob, stream=None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.prob = prob
+        self.n = _wl.STATE_DIM[prob["system"]]
+        self.m = _wl.CONTROL_DIM[prob["system"]]
+        self.K, self.T, self.q = prob["K"], prob["T"], prob["q"]
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.cfg = config_from_problem(prob)
+        self.ctx = mppi_jump_init(self.cfg, self.stream.cuda_stream)
+        with torch.cuda.stream(self.stream):
+            self.x0 = torch.zeros(self.n, dtype=torch.float32, device=self.device)
+            self.u0 = torch.zeros(self.m, dtype=torch.float32, device=self.device)
+
+    def close(self):
+        if self.ctx:
+            mppi_jump_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- data exchange -----------------------------------------------------
+    # Every tensor operation runs on the solver's stream, so that it is
+    # ordered with the library's work on that stream.
+    def _sync(self):
+        self.stream.synchronize()
+
+    def _on(self):
+        return self.torch.cuda.stream(self.stream)
+
+    def set_x0(self, x0):
+        with self._on():
+            self.x0.copy_(self.torch.as_tensor(np.asarray(x0, dtype=np.float32)), non_blocking=False)
+
+    def set_controls(self, U):
+        with self._on():
+            t = self.torch.as_tensor(np.ascontiguousarray(U, dtype=np.float32)).to(self.device)
+            mppi_jump_set_controls(self.ctx, t.data_ptr())
+        self._sync()
+
+    def controls(self):
+        with self._on():
+            t = self.torch.empty((self.T, self.m), dtype=self.torch.float32, device=self.device)
+            mppi_jump_get_controls(self.ctx, t.data_ptr())
+        self._sync()
+        return t.cpu().numpy()
+
+    def set_iteration(self, it):
+        mppi_jump_set_iteration(self.ctx, it)
+
+    def iteration(self):
+        return mppi_jump_get_iteration(self.ctx)
+
+    # -- the method ----------------------------------------------------------
+    def rollout_cost(self, x0, want_costs=True):
+        self.set_x0(x0)
+        costs = None
+        with self._on():
+            if want_costs:
+                costs = self.torch.empty(self.K, dtype=self.torch.float32, device=self.device)
+            mppi_jump_rollout_cost(self.ctx, self.x0.data_ptr(),
+                                   costs.data_ptr() if want_costs else 0)
+        return costs
+
+    def update(self):
+        mppi_jump_update(self.ctx)
+
+    def sync(self):
+        mppi_jump_sync(self.ctx)
+
+    def step(self, x0, iters=None):
+        x = np.ascontiguousarray(x0, dtype=np.float32)
+        u0 = np.zeros(self.m, dtype=np.float32)
+        mppi_jump_step(self.ctx, x, self.prob["iters"] if iters is None else iters, u0)
+        return u0
+
+    # -- debug copies -----------------------------------------------------
+    def enable_debug(self):
+        with self._on():
+            self.dbg_counts = self.torch.zeros((self.T, self.K), dtype=self.torch.uint8,
+                                               device=self.device)
+            self.dbg_J = self.torch.zeros((self.T, self.K, max(self.q, 1)),
+                                          dtype=self.torch.float32, device=self.device)
+        mppi_jump_set_debug(self.ctx, self.dbg_counts.data_ptr(), self.dbg_J.data_ptr())
+
+    def noise(self):
+        """delta_eff [T][K][m] as float32 numpy (bfloat16 values widened)."""
+        torch = self.torch
+        dt = torch.bfloat16 if self.prob["noise_dtype"] == "bf16" else torch.float32
+        with self._on():
+            t = torch.empty((self.T, self.K, self.m), dtype=dt, device=self.device)
+            mppi_jump_get_noise(self.ctx, t.data_ptr())
+        self._sync()
+        return t.float().cpu().numpy()
+
+    def noise_bits(self):
+        """Raw bfloat16 bit patterns of delta_eff (uint16 numpy), bf16 problems only."""
+        torch = self.torch
+        with self._on():
+            t = torch.empty((self.T, self.K, self.m), dtype=torch.int16, device=self.device)
+            mppi_jump_get_noise(self.ctx, t.data_ptr())
+        self._sync()
+        return t.cpu().numpy().view(np.uint16)
+
+    def weights(self):
+        with self._on():
+            t = self.torch.empty(self.K, dtype=self.torch.float32, device=self.device)
+            mppi_jump_get_weights(self.ctx, t.data_ptr())
+        self._sync()
+        return t.cpu().numpy()
+
+    def free_energy(self):
+        return mppi_jump_get_free_energy(self.ctx)
+
+    def get_state(self):
+        return mppi_jump_get_state(self.ctx)
+
+    def set_state(self, blob):
+        mppi_jump_set_state(self.ctx, blob)

@@ -1,0 +1,109 @@
+"""GPU parity: one MPPI iteration through the C ABI against the FP64 oracle,
+element by element, for the named workloads at full size and for ragged,
+tiny and mode-switching variants (see tests/parity.py for the tolerances)."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1807_06108_gb300 import workloads as W
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+REPORT = os.environ.get("MPPI_PARITY_REPORT")
+
+
+def _record(name, rep):
+    print(name, rep)
+    if REPORT:
+        with open(REPORT, "a") as f:
+            f.write(json.dumps({"case": name, **rep}) + "\n")
+
+
+def _obstacle_state(prob):
+    x = W.initial_state(prob).astype(np.float64)
+    x[0:3] = [1.45, 0.05, 1.0]
+    x[3] = 1.5
+    return x.astype(np.float32)
+
+
+def _cases():
+    rng = lambda s: np.random.default_rng(s)  # noqa: E731
+    c = {}
+    p = W.cartpole_k1000()
+    c["cartpole_K1000_T50"] = (p, W.initial_state(p), W.initial_controls(p), 0)
+    p = W.cartpole_k1000(K=777, T=23)
+    r = rng(1)
+    c["cartpole_K777_T23_random"] = (p, W.random_state(p, r), W.random_controls(p, r), 5)
+    p = W.cartpole_k1000(K=1500, T=31, nu=10.0, jump_channel="control", count_law="bernoulli",
+                         noise_dtype="bf16", c=2.0, mark_scale=1.0)
+    r = rng(2)
+    c["cartpole_bf16_control_bernoulli_c2"] = (p, W.random_state(p, r), W.random_controls(p, r), 9)
+    p = W.quadrotor_k4096()
+    c["quadrotor_K4096_T100"] = (p, W.initial_state(p), W.initial_controls(p), 0)
+    p = W.quadrotor_k4096(K=1000, T=37, lam=20.0)
+    r = rng(3)
+    c["quadrotor_K1000_T37_obstacle"] = (p, _obstacle_state(p), W.random_controls(p, r, 0.2), 3)
+    p = W.quadrotor_k4096(K=2053, T=45, nu=8.0, mark_law="laplace", noise_dtype="bf16",
+                          jump_sqrt_dt=True, lam=10.0)
+    r = rng(4)
+    c["quadrotor_laplace_bf16_sqrtdt"] = (p, W.random_state(p, r, 0.1), W.random_controls(p, r, 0.2), 1)
+    p = W.quadrotor_k4096(K=640, T=16, nu=6.0, jump_channel="control", c=2.0, lam=50.0,
+                          mark_scale=0.3, alpha=0.5)
+    r = rng(5)
+    c["quadrotor_control_c2_alpha05"] = (p, W.random_state(p, r, 0.1), W.random_controls(p, r, 0.2), 2)
+    p = W.cartpole_k1000(K=1, T=1)
+    c["cartpole_K1_T1"] = (p, W.initial_state(p), W.initial_controls(p), 0)
+    p = W.quadrotor_k4096(K=33, T=5, nu=50.0)
+    r = rng(6)
+    c["quadrotor_K33_T5_many_jumps"] = (p, W.random_state(p, r, 0.1), W.random_controls(p, r, 0.2), 77)
+    p = W.quadrotor_k4096(K=96, T=4096, dt=0.001, lam=100.0)
+    c["quadrotor_K96_T4096_max_horizon"] = (p, W.initial_state(p), W.initial_controls(p), 0)
+    p = W.cartpole_k1000(K=5000, T=50, nu=0.0)
+    c["cartpole_no_jumps"] = (p, W.initial_state(p), W.initial_controls(p), 4)
+    return c
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_iteration_matches_oracle(cuda, name):
+    prob, x0, U, it = CASES[name]
+    rep = parity.run_and_compare(prob, x0, U, it)
+    _record(name, rep)
+
+
+def test_large_quadrotor_sampled_and_full_update(cuda):
+    """K=65536, T=200, dt=0.005, Laplace marks at 5/s, bfloat16 noise: every
+    rollout's counts and noise, costs of rollouts 0..1023 and the full update
+    against the oracle over all K."""
+    prob = W.large_quadrotor()
+    x0, U = W.initial_state(prob), W.initial_controls(prob)
+    g = parity.gpu_iteration(prob, x0, U, 0)
+    r = parity.oracle_iteration(prob, x0, U, 0)
+    rep = parity.compare_iteration(prob, U, g, r)
+    _record("quadrotor_K65536_T200_bf16_laplace", rep)
+
+
+def test_all_costs_non_finite_leaves_controls(cuda):
+    from paper_1807_06108_gb300 import mppi
+    prob = W.cartpole_k1000(K=128, T=8)
+    x0 = np.array([np.nan, 0, 0, 0], dtype=np.float32)
+    U = W.random_controls(prob, np.random.default_rng(8))
+    s = mppi.Solver(prob)
+    try:
+        s.set_controls(U)
+        costs = s.rollout_cost(x0)
+        s.update()
+        with pytest.raises(mppi.MppiError) as e:
+            s.sync()
+        assert e.value.code == mppi.ENONFINITE
+        assert np.all(np.isinf(costs.cpu().numpy()))
+        np.testing.assert_array_equal(s.controls(), U)
+        s.sync()  # the status word was cleared
+    finally:
+        s.close()
