@@ -41,11 +41,14 @@ WORKLOADS = {
     "large_quadrotor": W.large_quadrotor,
 }
 
-# Source-level lane operations per trajectory step of the rollout kernel
-# (each 32-bit integer or float32 add / mul / fma / xor / compare / select
-# counts 1; log, exp and division 8, sqrt 4, sincos / sincospi 20), counted
-# from the sampling, cost and plant code of one step.
-ROLLOUT_OPS_PER_STEP = {"cartpole": 170.0, "quadrotor": 436.0}
+# Source-level lane operations per trajectory step (each 32-bit integer or
+# float32 add / mul / fma / xor / compare / select counts 1; the accurate log
+# 8, sqrt 4, sincospi 20; the hardware __sincosf 3 and __fdividef 2), counted
+# from the kernel source: SEQ = cost + plant + Euler step of the sequential
+# rollout kernel, NOISE = Philox, Box-Muller, perturbation and jump count of
+# the sampling kernel.  The fused tile does both in one kernel.
+SEQ_OPS_PER_STEP = {"cartpole": 64.0, "quadrotor": 154.0}
+NOISE_OPS_PER_STEP = {"cartpole": 79.0, "quadrotor": 218.0}
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -204,6 +207,9 @@ def run_ours(args):
     def one_step():
         mppi.mppi_jump_step_async(ctx, solver.x0.data_ptr(), iters, solver.u0.data_ptr())
 
+    # rollout tile chosen by the library's autotuner (U and counter restored)
+    tile, tile_ms = mppi.mppi_jump_autotune(ctx, solver.x0.data_ptr(), iters, reps=5)
+
     # warm-up (captures the graph)
     for _ in range(args.warmup):
         one_step()
@@ -260,7 +266,10 @@ def run_ours(args):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = n_sms * 128 * sm_mhz * 1e6 / 1e12  # T lane-ops/s
-    ops = ROLLOUT_OPS_PER_STEP[prob["system"]] * K * T
+    ops_step = SEQ_OPS_PER_STEP[prob["system"]]
+    if tile[0] == 1:
+        ops_step += NOISE_OPS_PER_STEP[prob["system"]]
+    ops = ops_step * K * T
     achieved = ops / (roll_avg / 1e3) / 1e12
     sb = 2 if prob["noise_dtype"] == "bf16" else 4
     m = solver.m
@@ -288,17 +297,23 @@ def run_ours(args):
         "config": {"workload": prob["name"], "K": K, "T": T, "iters": iters, "dt": prob["dt"],
                    "noise": prob["noise_dtype"], "jump_rate": prob["nu"],
                    "solves_per_s": value / steps_per_solve,
+                   "rollout_tile": {"variant": "fused" if tile[0] == 1 else "split",
+                                    "block": tile[1], "chunk": tile[2]},
                    "l2": "flushed between timed steps (write of 2x L2 size)"},
         "e2e": {"value": e2e, "unit": "trajectory-steps/s",
                 "h2d_bytes_per_step": 4 * solver.n, "d2h_bytes_per_step": 4 * m + 4,
                 "solves_per_s": e2e / steps_per_solve},
-        "gpu_launches": 4 * iters * args.steps,
-        "roofline": {"bound": "alu", "kernel": "rollout_kernel", "achieved": achieved,
+        # per iteration: noise + rollout + update kernels (split tile) or
+        # rollout + update (fused tile), timed region A only
+        "gpu_launches": (3 if tile[0] == 2 else 2) * iters * args.steps,
+        "roofline": {"bound": "alu",
+                     "kernel": "rollout_split_kernel" if tile[0] == 2 else "rollout_kernel",
+                     "achieved": achieved,
                      "peak": alu_peak, "unit": "T lane-ops/s", "frac": achieved / alu_peak,
                      "traffic": None, "avg_launch_ms": roll_avg,
                      "peak_basis": f"{n_sms} SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_kind} max clock)",
-                     "ops_per_trajectory_step": ROLLOUT_OPS_PER_STEP[prob["system"]]},
-        "roofline_update": {"bound": "hbm", "kernel": "softmin+update_partial+update_combine",
+                     "ops_per_trajectory_step": ops_step},
+        "roofline_update": {"bound": "hbm", "kernel": "update_kernel",
                             "achieved": upd_gbs, "peak": float(peaks.get("hbm_gbs", 6800.0)),
                             "unit": "GB/s", "frac": upd_gbs / float(peaks.get("hbm_gbs", 6800.0)),
                             "avg_launch_ms": upd_avg, "algorithmic_bytes": upd_bytes,

@@ -179,6 +179,34 @@ mppi_status mppi_jump_step(mppi_jump_ctx* ctx, const float* x0_host, int32_t ite
 mppi_status mppi_jump_step_async(mppi_jump_ctx* ctx, const float* x0, int32_t iters,
                                  float* u0);
 
+/* Rollout launch shape ("tile").  rollout_variant 1 = fused: one kernel,
+ * one thread per rollout, draws the noise and rolls out; 2 = split: a noise
+ * pass over K x T/4 threads stores delta_eff and the jump counts, then one
+ * thread per rollout runs the sequential dynamics (more parallelism when K
+ * alone does not fill the GPU).  rollout_block: threads per block of the
+ * rollout kernel (32, 64, 96 or 128).  rollout_chunk: steps per unrolled
+ * chunk of the split rollout, i.e. how many steps ahead its loads run (2, 4
+ * or 8; ignored by the fused variant).  Every tile computes identical
+ * results.  Setting a tile drops the cached graphs. */
+typedef struct {
+  int32_t rollout_variant;
+  int32_t rollout_block;
+  int32_t rollout_chunk;
+} mppi_jump_tuning;
+mppi_status mppi_jump_set_tuning(mppi_jump_ctx* ctx, const mppi_jump_tuning* tuning_host);
+mppi_status mppi_jump_get_tuning(mppi_jump_ctx* ctx, mppi_jump_tuning* tuning_host);
+
+/* Autotuner: times the MPC step (graph replay, `iters` iterations from the
+ * device state x0 [n]) for every rollout tile (fused x block 32, 64, 128;
+ * split x block 32, 64, 128 x chunk 2, 4, 8), `reps` timed steps each after
+ * one warm-up, with CUDA events on the
+ * context's stream, and keeps the fastest.  U and the iteration counter are
+ * restored afterwards, so tuning does not change later results (every tile
+ * computes the same values).  best_host (may be NULL) receives the choice and
+ * best_ms_host (may be NULL) its mean step time. */
+mppi_status mppi_jump_autotune(mppi_jump_ctx* ctx, const float* x0, int32_t iters, int32_t reps,
+                               mppi_jump_tuning* best_host, float* best_ms_host);
+
 /* Phase timing.  With timing enabled, each MPC step records CUDA events
  * around every rollout launch and every weights+update launch (event record
  * nodes inside the replayed graph); mppi_jump_phase_times synchronises and

@@ -26,6 +26,7 @@ struct DevPlant {
 struct DevProblem {
   int32_t system, K, Kpad, T, n, m, q;
   int32_t count_law, mark_law, jump_channel, nmax, noise_bf16;
+  int32_t jump_default;  // state jumps hit the plant's velocity rows (1, 3) / (3, 4, 5)
   int32_t jump_rows[4];
   uint32_t key0, key1;
   uint32_t thr[kMaxJumps];  // jump-count thresholds (see the header)
@@ -121,6 +122,10 @@ __device__ __forceinline__ void two_sum_merge(float& s, float& c, float s2, floa
 
 // ---------------------------------------------------------------------------
 // Plants: F(x, v) = f(x) + G(x) v (Eq. 4), Euler-stepped by the caller.
+// The trigonometric functions and reciprocals use the hardware approximations
+// (__sincosf: absolute error about 2^-21 for |x| <= pi; __fdividef: 2 ulp):
+// they sit on the sequential critical path of every step, and their error is
+// far below the float32-vs-float64 parity tolerance of the costs.
 // ---------------------------------------------------------------------------
 template <int SYS>
 struct Plant;
@@ -134,13 +139,14 @@ struct Plant<0> {
   __device__ __forceinline__ static void xdot(const DevPlant& p, const float* x, const float* v,
                                               float* xd) {
     float s, c;
-    sincosf(x[2], &s, &c);
+    __sincosf(x[2], &s, &c);
     const float thd = x[3];
     const float D = p.mc + p.mp * s * s;
     const float thd2 = thd * thd;
     const float f = v[0];
-    const float xdd = (f + p.mp * s * (p.l * thd2 + p.g * c)) / D;
-    const float thdd = (-f * c - p.mp * p.l * thd2 * c * s - p.mcp_g * s) / (p.l * D);
+    const float inv_D = __fdividef(1.0f, D);
+    const float xdd = (f + p.mp * s * (p.l * thd2 + p.g * c)) * inv_D;
+    const float thdd = (-f * c - p.mp * p.l * thd2 * c * s - p.mcp_g * s) * (inv_D * p.inv_l);
     xd[0] = x[1];
     xd[1] = xdd;
     xd[2] = thd;
@@ -176,9 +182,9 @@ struct Plant<1> {
   __device__ __forceinline__ static void xdot(const DevPlant& p, const float* x, const float* v,
                                               float* xd) {
     float sph, cph, sth, cth, sps, cps;
-    sincosf(x[6], &sph, &cph);
-    sincosf(x[7], &sth, &cth);
-    sincosf(x[8], &sps, &cps);
+    __sincosf(x[6], &sph, &cph);
+    __sincosf(x[7], &sth, &cth);
+    __sincosf(x[8], &sps, &cps);
     const float wp = x[9], wq = x[10], wr = x[11];
     const float a = (v[0] + v[1] + v[2] + v[3]) * p.inv_mass;
     xd[0] = x[3];
@@ -187,7 +193,7 @@ struct Plant<1> {
     xd[3] = a * (cph * sth * cps + sph * sps);
     xd[4] = a * (cph * sth * sps - sph * cps);
     xd[5] = a * (cph * cth) - p.qg;
-    const float inv_cth = 1.0f / cth;
+    const float inv_cth = __fdividef(1.0f, cth);
     const float tth = sth * inv_cth;
     xd[6] = wp + sph * tth * wq + cph * tth * wr;
     xd[7] = cph * wq - sph * wr;

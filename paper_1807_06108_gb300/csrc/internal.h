@@ -1,6 +1,6 @@
 // internal.h -- host-side helpers shared by the translation units of
 // libmppi_jump.so (configuration checks, device-problem packing, launch
-// geometry).  Not part of the public ABI.
+// geometry, kernel launches).  Not part of the public ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -34,30 +34,62 @@ struct UpdateGeom {
 };
 UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms);
 
-// Per-process kernel attributes (dynamic shared memory limits); call on the
-// current device before the first launch or stream capture.
+// Per-process kernel attributes; call on the current device before the first
+// launch or stream capture.
 cudaError_t prepare_kernels();
 
-// Enqueue the kernels of one iteration for a single problem.  it_ptr and the
-// other pointers are device pointers; shift != 0 performs the MPC shift and
-// writes u0 (if not NULL) after the update.
+// Rollout launch shape: variant 1 = fused (one kernel draws and rolls out),
+// 2 = split (noise_kernel over K*T/4 threads, then rollout_split_kernel);
+// block = threads per block of the rollout kernel; chunk = steps per unrolled
+// chunk of the split rollout (its load-ahead depth: 2, 4 or 8).
+struct RolloutTile {
+  int variant;
+  int block;
+  int chunk;
+};
+RolloutTile default_tile(const DevProblem& P, int num_sms);
+bool valid_tile(const RolloutTile& t);
+
+// Device buffers of one problem (one noise set; the MPC step alternates two).
 struct IterBuffers {
   const float* x0;
   float* U;
-  void* noise;
-  float* s_part;
-  float* w;
-  float* partial;
-  float* cconst;
-  float* diag;
+  void* noise;         // [T][Kpad][m] delta_eff, float32 or bfloat16
+  uint8_t* counts;     // [T][Kpad] jump counts
+  float4* jrec;        // [T][Kpad] state-jump step records (split variant)
+  float* s_part;       // [Kpad] k-dependent cost part
+  float* w;            // [Kpad] unnormalised weights e_k
+  float* partial;      // [chunks][T][m]
+  float* zpart;        // [chunks]
+  uint32_t* rho_key;   // running minimum of the costs (order key)
+  unsigned* done;      // completion ticket of the update
+  float* cconst;       // k-independent cost term
+  float* diag;         // rho, Z, F
   int* status;
-  uint32_t* it;
+  uint32_t* it;        // iteration counter at the start of the step
   float* costs;        // may be NULL
   uint8_t* dbg_counts; // may be NULL
   float* dbg_J;        // may be NULL
 };
-cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, cudaStream_t s);
-cudaError_t launch_weights_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g,
-                                  int shift, float* u0, cudaStream_t s);
+
+// Split variant, part 1: noise of iteration *it + it_off into b.noise etc.
+cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s);
+// Split variant, part 2: the sequential rollout over the stored noise.
+cudaError_t launch_rollout_seq(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
+                               cudaStream_t s);
+// Whole rollout (either variant) of iteration *it + it_off.  arm_min resets
+// the running cost minimum first (the update re-arms it after every
+// iteration, so only a rollout that follows no update needs it).
+cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
+                           uint32_t it_off, bool arm_min, cudaStream_t s);
+// Weights + update; shift != 0 performs the MPC shift and writes u0 (if not
+// NULL); the counter advances by it_advance.
+cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g, int shift,
+                          uint32_t it_advance, float* u0, cudaStream_t s);
+// costs[k] = S~_k (the full augmented cost) when b.costs is not NULL.
+cudaError_t launch_costs(const DevProblem& P, const IterBuffers& b, cudaStream_t s);
+// w_k = e_k / Z (Z = diag[1]) for the weights getter.
+cudaError_t launch_normalize_weights(const float* e, const float* diag, int K, float* w,
+                                     cudaStream_t s);
 
 }  // namespace mj

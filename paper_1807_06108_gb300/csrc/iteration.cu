@@ -74,6 +74,15 @@ mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg) 
   P->jump_channel = cfg->jump_channel;
   P->nmax = nmax;
   P->noise_bf16 = cfg->noise_dtype == MPPI_NOISE_BF16;
+  // the plant's velocity rows get a specialised jump update
+  P->jump_default = 0;
+  if (cfg->jump_channel == MPPI_JUMP_STATE) {
+    if (cfg->system == MPPI_CARTPOLE)
+      P->jump_default = cfg->q == 2 && cfg->jump_rows[0] == 1 && cfg->jump_rows[1] == 3;
+    else
+      P->jump_default = cfg->q == 3 && cfg->jump_rows[0] == 3 && cfg->jump_rows[1] == 4 &&
+                        cfg->jump_rows[2] == 5;
+  }
   for (int c = 0; c < 4; ++c) P->jump_rows[c] = c < cfg->q ? cfg->jump_rows[c] : -1;
   P->key0 = (uint32_t)(cfg->seed & 0xffffffffull);
   P->key1 = (uint32_t)(cfg->seed >> 32);
@@ -134,12 +143,7 @@ mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg) 
   return MPPI_OK;
 }
 
-cudaError_t prepare_kernels() {
-  // the combine kernel keeps the whole sequence (up to 4096 x 4 floats) in
-  // shared memory; idempotent, called before any launch or capture
-  return cudaFuncSetAttribute(update_combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              4096 * 4 * (int)sizeof(float));
-}
+cudaError_t prepare_kernels() { return cudaSuccess; }
 
 UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms) {
   UpdateGeom g;
@@ -147,7 +151,9 @@ UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms) {
   const int nvec = Kpad * m / E;
   g.vpt = nvec >= 4 * kUpdateThreads ? 4 : (nvec >= 2 * kUpdateThreads ? 2 : 1);
   g.chunks = (nvec + kUpdateThreads * g.vpt - 1) / (kUpdateThreads * g.vpt);
-  const int target = 2 * (num_sms > 0 ? num_sms : 152);
+  // enough blocks to cover every SM several times over: at small K each block
+  // is short, and latency (not bandwidth) sets the update's duration
+  const int target = 4 * (num_sms > 0 ? num_sms : 152);
   int groups = (target + g.chunks - 1) / g.chunks;
   if (groups > T) groups = T;
   if (groups < 1) groups = 1;
@@ -156,59 +162,168 @@ UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms) {
   return g;
 }
 
-template <int SYS, bool BF16, bool DBG>
-static void launch_rollout_t(const DevProblem& P, const IterBuffers& b, cudaStream_t s) {
-  const int blocks = (P.Kpad + kRolloutThreads - 1) / kRolloutThreads;
-  rollout_kernel<SYS, BF16, DBG><<<blocks, kRolloutThreads, 0, s>>>(
-      P, b.x0, b.U, b.it, b.s_part, b.costs, b.cconst, b.noise, b.dbg_counts, b.dbg_J);
+RolloutTile default_tile(const DevProblem& P, int num_sms) {
+  (void)P;
+  (void)num_sms;
+  RolloutTile t;
+  t.variant = 2;
+  t.block = 128;
+  t.chunk = 4;
+  return t;
 }
 
-cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, cudaStream_t s) {
+bool valid_tile(const RolloutTile& t) {
+  return (t.variant == 1 || t.variant == 2) && t.block >= 32 && t.block <= kRolloutThreads &&
+         t.block % 32 == 0 && (t.chunk == 2 || t.chunk == 4 || t.chunk == 8);
+}
+
+template <int M, bool BF16, bool DBG>
+static void launch_noise_t(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s) {
+  const long long nthreads = (long long)P.Kpad * ((P.T + 3) / 4);
+  const int nblocks = (int)((nthreads + kNoiseThreads - 1) / kNoiseThreads);
+  noise_kernel<M, BF16, DBG><<<nblocks, kNoiseThreads, 0, s>>>(
+      P, b.it, it_off, b.noise, b.counts, b.jrec, b.dbg_counts, b.dbg_J);
+}
+
+cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s) {
   const bool dbg = b.dbg_counts != nullptr || b.dbg_J != nullptr;
-  const int sel = P.system * 4 + (P.noise_bf16 ? 2 : 0) + (dbg ? 1 : 0);
+  const int sel = (P.m == 4 ? 4 : 0) + (P.noise_bf16 ? 2 : 0) + (dbg ? 1 : 0);
   switch (sel) {
-    case 0: launch_rollout_t<0, false, false>(P, b, s); break;
-    case 1: launch_rollout_t<0, false, true>(P, b, s); break;
-    case 2: launch_rollout_t<0, true, false>(P, b, s); break;
-    case 3: launch_rollout_t<0, true, true>(P, b, s); break;
-    case 4: launch_rollout_t<1, false, false>(P, b, s); break;
-    case 5: launch_rollout_t<1, false, true>(P, b, s); break;
-    case 6: launch_rollout_t<1, true, false>(P, b, s); break;
-    default: launch_rollout_t<1, true, true>(P, b, s); break;
+    case 0: launch_noise_t<1, false, false>(P, b, it_off, s); break;
+    case 1: launch_noise_t<1, false, true>(P, b, it_off, s); break;
+    case 2: launch_noise_t<1, true, false>(P, b, it_off, s); break;
+    case 3: launch_noise_t<1, true, true>(P, b, it_off, s); break;
+    case 4: launch_noise_t<4, false, false>(P, b, it_off, s); break;
+    case 5: launch_noise_t<4, false, true>(P, b, it_off, s); break;
+    case 6: launch_noise_t<4, true, false>(P, b, it_off, s); break;
+    default: launch_noise_t<4, true, true>(P, b, it_off, s); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int SYS, bool BF16>
+static void launch_seq_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
+                         cudaStream_t s) {
+  const int blocks = (P.Kpad + tile.block - 1) / tile.block;
+  if (tile.chunk == 2)
+    rollout_split_kernel<SYS, BF16, 2><<<blocks, tile.block, 0, s>>>(
+        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
+  else if (tile.chunk == 8)
+    rollout_split_kernel<SYS, BF16, 8><<<blocks, tile.block, 0, s>>>(
+        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
+  else
+    rollout_split_kernel<SYS, BF16, 4><<<blocks, tile.block, 0, s>>>(
+        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
+}
+
+cudaError_t launch_rollout_seq(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
+                               cudaStream_t s) {
+  if (!valid_tile(tile)) return cudaErrorInvalidValue;
+  switch (P.system * 2 + (P.noise_bf16 ? 1 : 0)) {
+    case 0: launch_seq_t<0, false>(P, b, tile, s); break;
+    case 1: launch_seq_t<0, true>(P, b, tile, s); break;
+    case 2: launch_seq_t<1, false>(P, b, tile, s); break;
+    default: launch_seq_t<1, true>(P, b, tile, s); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int SYS, bool BF16, bool DBG>
+static void launch_fused_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
+                           uint32_t it_off, cudaStream_t s) {
+  const int blocks = (P.Kpad + tile.block - 1) / tile.block;
+  rollout_kernel<SYS, BF16, DBG><<<blocks, tile.block, 0, s>>>(
+      P, b.x0, b.U, b.it, it_off, b.s_part, b.noise, b.rho_key, b.dbg_counts, b.dbg_J);
+}
+
+cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
+                           uint32_t it_off, bool arm_min, cudaStream_t s) {
+  if (!valid_tile(tile)) return cudaErrorInvalidValue;
+  if (arm_min) {
+    cudaError_t e = cudaMemsetAsync(b.rho_key, 0xff, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+  }
+  if (tile.variant == 2) {
+    cudaError_t e = launch_noise(P, b, it_off, s);
+    if (e != cudaSuccess) return e;
+    return launch_rollout_seq(P, b, tile, s);
+  }
+  const bool dbg = b.dbg_counts != nullptr || b.dbg_J != nullptr;
+  switch (P.system * 4 + (P.noise_bf16 ? 2 : 0) + (dbg ? 1 : 0)) {
+    case 0: launch_fused_t<0, false, false>(P, b, tile, it_off, s); break;
+    case 1: launch_fused_t<0, false, true>(P, b, tile, it_off, s); break;
+    case 2: launch_fused_t<0, true, false>(P, b, tile, it_off, s); break;
+    case 3: launch_fused_t<0, true, true>(P, b, tile, it_off, s); break;
+    case 4: launch_fused_t<1, false, false>(P, b, tile, it_off, s); break;
+    case 5: launch_fused_t<1, false, true>(P, b, tile, it_off, s); break;
+    case 6: launch_fused_t<1, true, false>(P, b, tile, it_off, s); break;
+    default: launch_fused_t<1, true, true>(P, b, tile, it_off, s); break;
   }
   return cudaGetLastError();
 }
 
 template <bool BF16, int M, int VPT>
-static void launch_partial_t(const IterBuffers& b, const UpdateGeom& g, int Kpad, int T,
-                             cudaStream_t s) {
-  dim3 grid(g.chunks, g.groups);
-  update_partial_kernel<BF16, M, VPT><<<grid, kUpdateThreads, 0, s>>>(b.noise, b.w, Kpad, T, g.rows,
-                                                                      b.partial, b.status);
+static void launch_update_t(const UpdateArgs& a, const UpdateGeom& g, cudaStream_t s) {
+  update_kernel<BF16, M, VPT><<<dim3(g.chunks, g.groups), kUpdateThreads, 0, s>>>(a);
 }
 
 template <bool BF16, int M>
-static void launch_partial_m(const IterBuffers& b, const UpdateGeom& g, int Kpad, int T,
-                             cudaStream_t s) {
-  if (g.vpt == 4) launch_partial_t<BF16, M, 4>(b, g, Kpad, T, s);
-  else if (g.vpt == 2) launch_partial_t<BF16, M, 2>(b, g, Kpad, T, s);
-  else launch_partial_t<BF16, M, 1>(b, g, Kpad, T, s);
+static void launch_update_m(const UpdateArgs& a, const UpdateGeom& g, cudaStream_t s) {
+  if (g.vpt == 4) launch_update_t<BF16, M, 4>(a, g, s);
+  else if (g.vpt == 2) launch_update_t<BF16, M, 2>(a, g, s);
+  else launch_update_t<BF16, M, 1>(a, g, s);
 }
 
-cudaError_t launch_weights_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g,
-                                  int shift, float* u0, cudaStream_t s) {
-  softmin_kernel<<<1, kSoftminThreads, 0, s>>>(b.s_part, P.K, P.Kpad, P.inv_lam, b.cconst, b.w,
-                                                b.diag, b.status);
+cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g, int shift,
+                          uint32_t it_advance, float* u0, cudaStream_t s) {
+  UpdateArgs a;
+  a.noise = b.noise;
+  a.s_part = b.s_part;
+  a.K = P.K;
+  a.Kpad = P.Kpad;
+  a.T = P.T;
+  a.rows = g.rows;
+  a.inv_lam = P.inv_lam;
+  a.lam = P.lam;
+  a.alpha = P.alpha;
+  for (int i = 0; i < 4; ++i) a.inv_sigma2[i] = P.inv_sigma2[i];
+  a.partial = b.partial;
+  a.zpart = b.zpart;
+  a.e_out = b.w;
+  a.U = b.U;
+  a.u0_out = u0;
+  a.diag = b.diag;
+  a.status = b.status;
+  a.done = b.done;
+  a.rho_key = b.rho_key;
+  a.it = b.it;
+  a.it_advance = it_advance;
+  a.shift = shift;
+  for (int i = 0; i < 4; ++i) a.u_init[i] = P.u_init[i];
   if (P.m == 4) {
-    if (P.noise_bf16) launch_partial_m<true, 4>(b, g, P.Kpad, P.T, s);
-    else launch_partial_m<false, 4>(b, g, P.Kpad, P.T, s);
+    if (P.noise_bf16) launch_update_m<true, 4>(a, g, s);
+    else launch_update_m<false, 4>(a, g, s);
   } else {
-    if (P.noise_bf16) launch_partial_m<true, 1>(b, g, P.Kpad, P.T, s);
-    else launch_partial_m<false, 1>(b, g, P.Kpad, P.T, s);
+    if (P.noise_bf16) launch_update_m<true, 1>(a, g, s);
+    else launch_update_m<false, 1>(a, g, s);
   }
-  const size_t smem = (size_t)P.T * P.m * sizeof(float);
-  update_combine_kernel<<<1, kCombineThreads, smem, s>>>(b.partial, g.chunks, P.T, P.m, P.alpha, b.U,
-                                                         b.status, b.it, shift, P, u0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_costs(const DevProblem& P, const IterBuffers& b, cudaStream_t s) {
+  if (!b.costs) return cudaSuccess;
+  const float4 is2 = make_float4(P.inv_sigma2[0], P.inv_sigma2[1], P.inv_sigma2[2], P.inv_sigma2[3]);
+  const int blocks = (P.K + kUpdateThreads - 1) / kUpdateThreads;
+  if (P.m == 4)
+    costs_kernel<4><<<blocks, kUpdateThreads, 0, s>>>(b.U, P.T, P.lam, is2, b.s_part, P.K, b.costs);
+  else
+    costs_kernel<1><<<blocks, kUpdateThreads, 0, s>>>(b.U, P.T, P.lam, is2, b.s_part, P.K, b.costs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize_weights(const float* e, const float* diag, int K, float* w,
+                                     cudaStream_t s) {
+  normalize_weights_kernel<<<(K + 255) / 256, 256, 0, s>>>(e, diag, K, w);
   return cudaGetLastError();
 }
 

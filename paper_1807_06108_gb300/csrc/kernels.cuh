@@ -1,8 +1,12 @@
-// kernels.cuh -- the four kernels of one MPPI iteration on jump diffusions:
-//   rollout_kernel        sampling + rollout + augmented cost (A1+A2)
-//   softmin_kernel        free-energy weights (A3)
-//   update_partial_kernel split-K weighted sum of the perturbations (A4)
-//   update_combine_kernel fixed-order combine, U update, counter, MPC shift (A4/A5)
+// kernels.cuh -- the kernels of one MPPI iteration on jump diffusions:
+//   rollout_kernel        fused sampling + rollout + augmented cost (A1+A2)
+//   noise_kernel          split form, part 1: sampling over K x T/4 threads (A1)
+//   rollout_split_kernel  split form, part 2: sequential rollout + cost (A2)
+//   update_kernel         free-energy weights, split-K weighted sum, combine,
+//                         U update, counter and MPC shift (A3+A4+A5)
+// Both rollout forms publish min_k S~_k through one atomic per warp.  The
+// random stream of an iteration is selected by *it_ptr + it_off, so the noise
+// of a later iteration can be drawn while the current one is still rolled out.
 // Included by the translation units that launch them.
 #pragma once
 
@@ -11,42 +15,189 @@
 namespace mj {
 
 constexpr int kRolloutThreads = 128;
-constexpr int kSoftminThreads = 1024;
+constexpr int kNoiseThreads = 128;
 constexpr int kUpdateThreads = 256;
-constexpr int kCombineThreads = 1024;
 constexpr int kStatusNonFinite = 5;
+constexpr uint32_t kKeyEmpty = 0xffffffffu;  // larger than every cost key
+constexpr uint32_t kKeyInf = 0xff800000u;    // order key of +inf
 
 // ---------------------------------------------------------------------------
-// Rollout: one thread per rollout k, the plant state in registers.  Per step
-// j: the Gaussian perturbation (stream 0), the jump count (stream 1, one
+// Order-preserving map between float32 and uint32 (an atomic minimum over
+// costs of either sign): larger key <=> larger float.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t order_key(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_to_float(uint32_t key) {
+  return __uint_as_float((key & 0x80000000u) ? (key & 0x7fffffffu) : ~key);
+}
+
+// Warp minimum of the rollout costs folded into a global atomic minimum (one
+// atomic per warp).  Every lane of the warp must call it.
+__device__ __forceinline__ void publish_min_cost(float sk, uint32_t* rho_key) {
+  const uint32_t w = __reduce_min_sync(0xffffffffu, order_key(sk));
+  if ((threadIdx.x & 31) == 0) atomicMin(rho_key, w);
+}
+
+// Summed marks of the jumps of one step (streams 2+n of the Philox counter).
+__device__ __forceinline__ void draw_marks(const DevProblem& P, uint32_t k, uint32_t j, uint32_t it,
+                                           int N, float J[4]) {
+  for (int nj = 0; nj < N; ++nj) {
+    const uint4 wm = philox4x32_10(k, j, it, 2u + (uint32_t)nj, P.key0, P.key1);
+    if (P.mark_law == 0) {
+      float z[4];
+      normals4(wm, z);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < P.q) J[c] += P.mark_scale[c] * z[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < P.q) J[c] += laplace_mark(P.mark_scale[c], word_of(wm, c));
+    }
+  }
+}
+
+template <int M, bool BF16>
+__device__ __forceinline__ void store_noise(void* __restrict__ noise, size_t row, const float* de,
+                                            bool active) {
+  if constexpr (BF16) {
+    if constexpr (M == 4) {
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(active ? de[0] : 0.0f, active ? de[1] : 0.0f);
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(active ? de[2] : 0.0f, active ? de[3] : 0.0f);
+      uint2 pk;
+      pk.x = *reinterpret_cast<const uint32_t*>(&lo);
+      pk.y = *reinterpret_cast<const uint32_t*>(&hi);
+      reinterpret_cast<uint2*>(noise)[row] = pk;
+    } else {
+      reinterpret_cast<__nv_bfloat16*>(noise)[row] = __float2bfloat16_rn(active ? de[0] : 0.0f);
+    }
+  } else {
+    if constexpr (M == 4) {
+      reinterpret_cast<float4*>(noise)[row] = active ? make_float4(de[0], de[1], de[2], de[3])
+                                                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    } else {
+      reinterpret_cast<float*>(noise)[row] = active ? de[0] : 0.0f;
+    }
+  }
+}
+
+template <int M, bool BF16>
+__device__ __forceinline__ void load_noise(const void* __restrict__ noise, size_t row, float* de) {
+  if constexpr (BF16) {
+    if constexpr (M == 4) {
+      const uint2 pk = reinterpret_cast<const uint2*>(noise)[row];
+      de[0] = __uint_as_float(pk.x << 16);
+      de[1] = __uint_as_float(pk.x & 0xffff0000u);
+      de[2] = __uint_as_float(pk.y << 16);
+      de[3] = __uint_as_float(pk.y & 0xffff0000u);
+    } else {
+      const unsigned short h = reinterpret_cast<const unsigned short*>(noise)[row];
+      de[0] = __uint_as_float((uint32_t)h << 16);
+    }
+  } else {
+    if constexpr (M == 4) {
+      const float4 v = reinterpret_cast<const float4*>(noise)[row];
+      de[0] = v.x;
+      de[1] = v.y;
+      de[2] = v.z;
+      de[3] = v.w;
+    } else {
+      de[0] = reinterpret_cast<const float*>(noise)[row];
+    }
+  }
+}
+
+// One step of cost and dynamics shared by both rollout forms: the
+// k-dependent part of the augmented running cost of Eq. 34-35 in control
+// units (the term lambda/2 u^T Sigma^-1 u is the same for every rollout and
+// cancels in the weights; it is summed once per iteration by
+// control_cost_sum), the Euler step of Algorithm 1 with the control-affine
+// drift of Eq. 4, then the state jump when the step has one.
+template <int SYS>
+__device__ __forceinline__ void cost_and_step(const DevProblem& P, float* x, const float* u,
+                                              const float* de, bool jumped, const float J[4],
+                                              float& s, float& sc) {
+  using PL = Plant<SYS>;
+  constexpr int n = PL::n, m = PL::m;
+  float uSd = 0.0f, dSd = 0.0f;
+#pragma unroll
+  for (int i = 0; i < m; ++i) {
+    const float ad = P.inv_sigma2[i] * de[i];
+    uSd += u[i] * ad;
+    dSd += de[i] * ad;
+  }
+  const float qx = PL::state_cost(P.pl, x);
+  two_sum_acc(s, sc, qx * P.dt + P.lam * (uSd + P.is_coef * dSd));
+  float v[m], xd[n];
+#pragma unroll
+  for (int i = 0; i < m; ++i) v[i] = u[i] + de[i];
+  PL::xdot(P.pl, x, v, xd);
+#pragma unroll
+  for (int i = 0; i < n; ++i) x[i] += xd[i] * P.dt;
+  if (jumped && P.jump_channel == 0) {
+    if (P.jump_default) {
+      // the plant's velocity rows: (xdot, thetadot) or (vx, vy, vz)
+      if constexpr (SYS == 0) {
+        x[1] += P.s_jump * J[0];
+        x[3] += P.s_jump * J[1];
+      } else {
+        x[3] += P.s_jump * J[0];
+        x[4] += P.s_jump * J[1];
+        x[5] += P.s_jump * J[2];
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < n; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < P.q && P.jump_rows[c] == r) x[r] += P.s_jump * J[c];
+    }
+  }
+}
+
+// Final cost of a rollout: terminal cost, non-finite -> +inf, and the warp's
+// contribution to the running minimum.
+template <int SYS>
+__device__ __forceinline__ void finish_rollout(const DevProblem& P, int k, bool active, const float* x,
+                                               float s, float sc, float* __restrict__ s_part,
+                                               uint32_t* __restrict__ rho_key) {
+  two_sum_acc(s, sc, Plant<SYS>::terminal_cost(P.pl, x));
+  float sk = s + sc;
+  if (!isfinite(sk) || !active) sk = INFINITY;
+  s_part[k] = sk;
+  publish_min_cost(sk, rho_key);  // Kpad is a multiple of 32: whole warps
+}
+
+
+// ---------------------------------------------------------------------------
+// Fused rollout: one thread per rollout k, the plant state in registers.  Per
+// step j: the Gaussian perturbation (stream 0), the jump count (stream 1, one
 // Philox block per four steps) and, when the count is positive, the marks
 // (streams 2+n); delta_eff is rounded to bfloat16 first when the noise is
-// stored in that type, so the rollout uses exactly the stored value; the
-// augmented cost of Eq. 34-35 is accumulated with compensated summation and
-// the k-independent term lambda/2 u^T Sigma^-1 u is kept apart (it cancels in
-// the weights); the Euler step adds the state jump.  delta_eff is stored
-// step-major, noise[(j*Kpad + k)*m + i], so each warp store is contiguous.
-// Rollouts K..Kpad-1 (padding) store zero noise and an infinite cost.
+// stored in that type, so the rollout uses exactly the stored value; then
+// cost_and_step.  delta_eff is stored step-major, noise[(j*Kpad + k)*m + i],
+// so each warp store is contiguous.  Rollouts K..Kpad-1 (padding) store zero
+// noise and an infinite cost.
 // ---------------------------------------------------------------------------
 template <int SYS, bool BF16, bool DBG>
 __global__ void __launch_bounds__(kRolloutThreads)
 rollout_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
-               const uint32_t* __restrict__ it_ptr, float* __restrict__ s_part,
-               float* __restrict__ costs, float* __restrict__ cconst, void* __restrict__ noise,
-               uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J) {
-  using PL = Plant<SYS>;
-  constexpr int n = PL::n, m = PL::m;
+               const uint32_t* __restrict__ it_ptr, uint32_t it_off, float* __restrict__ s_part,
+               void* __restrict__ noise,
+               uint32_t* __restrict__ rho_key, uint8_t* __restrict__ dbg_counts,
+               float* __restrict__ dbg_J) {
+  constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P.Kpad) return;
   const bool active = k < P.K;
-  const uint32_t it = __ldg(it_ptr);
+  const uint32_t it = __ldg(it_ptr) + it_off;
   const uint32_t uk = (uint32_t)k;
-
   float x[n];
 #pragma unroll
   for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
-  float s = 0.0f, sc = 0.0f, C = 0.0f, Cc = 0.0f;
-
+  float s = 0.0f, sc = 0.0f;
   for (int j0 = 0; j0 < P.T; j0 += 4) {
     const uint4 wcount = philox4x32_10(uk, (uint32_t)(j0 >> 2), it, 1u, P.key0, P.key1);
     float zc[4];
@@ -67,20 +218,7 @@ rollout_kernel(const DevProblem P, const float* __restrict__ x0, const float* __
       const int N = jump_count(P, word_of(wcount, jj));
       float J[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       if (N > 0) {
-        for (int nj = 0; nj < N; ++nj) {
-          const uint4 wm = philox4x32_10(uk, (uint32_t)j, it, 2u + (uint32_t)nj, P.key0, P.key1);
-          if (P.mark_law == 0) {
-            float z[4];
-            normals4(wm, z);
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-              if (c < P.q) J[c] += P.mark_scale[c] * z[c];
-          } else {
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-              if (c < P.q) J[c] += laplace_mark(P.mark_scale[c], word_of(wm, c));
-          }
-        }
+        draw_marks(P, uk, (uint32_t)j, it, N, J);
         if (P.jump_channel == 1) {
 #pragma unroll
           for (int i = 0; i < m; ++i) de[i] += J[i];
@@ -90,55 +228,11 @@ rollout_kernel(const DevProblem P, const float* __restrict__ x0, const float* __
 #pragma unroll
         for (int i = 0; i < m; ++i) de[i] = __bfloat162float(__float2bfloat16_rn(de[i]));
       }
-      // augmented running cost (Eq. 34-35 in control units)
       float u[m];
-      float uSu = 0.0f, uSd = 0.0f, dSd = 0.0f;
 #pragma unroll
-      for (int i = 0; i < m; ++i) {
-        u[i] = __ldg(U + j * m + i);
-        const float a = P.inv_sigma2[i];
-        uSu += u[i] * a * u[i];
-        uSd += u[i] * a * de[i];
-        dSd += de[i] * a * de[i];
-      }
-      const float qx = PL::state_cost(P.pl, x);
-      two_sum_acc(s, sc, qx * P.dt + P.lam * (uSd + P.is_coef * dSd));
-      two_sum_acc(C, Cc, 0.5f * P.lam * uSu);
-      // Euler step (Algorithm 1) with the control-affine drift (Eq. 4)
-      float v[m], xd[n];
-#pragma unroll
-      for (int i = 0; i < m; ++i) v[i] = u[i] + de[i];
-      PL::xdot(P.pl, x, v, xd);
-#pragma unroll
-      for (int i = 0; i < n; ++i) x[i] += xd[i] * P.dt;
-      if (N > 0 && P.jump_channel == 0) {
-#pragma unroll
-        for (int r = 0; r < n; ++r)
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (c < P.q && P.jump_rows[c] == r) x[r] += P.s_jump * J[c];
-      }
-      // store delta_eff, step-major
-      const size_t row = (size_t)j * P.Kpad + k;
-      if constexpr (BF16) {
-        if constexpr (m == 4) {
-          const __nv_bfloat162 lo = __floats2bfloat162_rn(active ? de[0] : 0.0f, active ? de[1] : 0.0f);
-          const __nv_bfloat162 hi = __floats2bfloat162_rn(active ? de[2] : 0.0f, active ? de[3] : 0.0f);
-          uint2 pk;
-          pk.x = *reinterpret_cast<const uint32_t*>(&lo);
-          pk.y = *reinterpret_cast<const uint32_t*>(&hi);
-          reinterpret_cast<uint2*>(noise)[row] = pk;
-        } else {
-          reinterpret_cast<__nv_bfloat16*>(noise)[row] = __float2bfloat16_rn(active ? de[0] : 0.0f);
-        }
-      } else {
-        if constexpr (m == 4) {
-          reinterpret_cast<float4*>(noise)[row] = active ? make_float4(de[0], de[1], de[2], de[3])
-                                                         : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        } else {
-          reinterpret_cast<float*>(noise)[row] = active ? de[0] : 0.0f;
-        }
-      }
+      for (int i = 0; i < m; ++i) u[i] = __ldg(U + j * m + i);
+      cost_and_step<SYS>(P, x, u, de, N > 0, J, s, sc);
+      store_noise<m, BF16>(noise, (size_t)j * P.Kpad + k, de, active);
       if (DBG && active) {
         const size_t rk = (size_t)j * P.K + k;
         if (dbg_counts) dbg_counts[rk] = (uint8_t)N;
@@ -147,28 +241,141 @@ rollout_kernel(const DevProblem P, const float* __restrict__ x0, const float* __
       }
     }
   }
-  two_sum_acc(s, sc, PL::terminal_cost(P.pl, x));
-  if (active) {
-    float sk = s + sc;
-    if (!isfinite(sk)) sk = INFINITY;
-    s_part[k] = sk;
-    const float cc = C + Cc;
-    if (costs) costs[k] = cc + sk;
-    if (k == 0) *cconst = cc;
-  } else {
-    s_part[k] = INFINITY;
+  finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
+}
+
+// ---------------------------------------------------------------------------
+// Split form, part 1.  noise_kernel: thread (k, b) draws steps 4b .. 4b+3 of
+// rollout k (the four steps that share one jump-count Philox block), so the
+// sampling runs over K * T/4 threads instead of K.  It stores delta_eff (the
+// control-channel jumps folded in, the bfloat16 rounding applied), the jump
+// counts counts[j*Kpad + k] and, for state-channel jumps, a 16-byte step
+// record jrec[j*Kpad + k] = (J_0, J_1, J_2, N) (or (J_0..J_3) when q = 4);
+// consecutive threads take consecutive k, so every store is contiguous.  It
+// touches nothing the rollout or update of another iteration reads, so it can
+// run concurrently with them on a second buffer set.
+// ---------------------------------------------------------------------------
+template <int M, bool BF16, bool DBG>
+__global__ void __launch_bounds__(kNoiseThreads)
+noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t it_off,
+             void* __restrict__ noise, uint8_t* __restrict__ counts, float4* __restrict__ jrec,
+             uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J) {
+  const int nb = (P.T + 3) >> 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P.Kpad * nb) return;
+  const int k = t % P.Kpad, b = t / P.Kpad;
+  const bool active = k < P.K;
+  const uint32_t it = __ldg(it_ptr) + it_off;
+  const uint32_t uk = (uint32_t)k;
+  const uint4 wcount = philox4x32_10(uk, (uint32_t)b, it, 1u, P.key0, P.key1);
+  float zc[4];
+  if constexpr (M == 1) normals4(philox4x32_10(uk, (uint32_t)b, it, 0u, P.key0, P.key1), zc);
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int j = 4 * b + jj;
+    if (j >= P.T) break;
+    float de[M];
+    if constexpr (M == 1) {
+      de[0] = P.sqc_sigma[0] * zc[jj];
+    } else {
+      float z[4];
+      normals4(philox4x32_10(uk, (uint32_t)j, it, 0u, P.key0, P.key1), z);
+#pragma unroll
+      for (int i = 0; i < M; ++i) de[i] = P.sqc_sigma[i] * z[i];
+    }
+    const int N = jump_count(P, word_of(wcount, jj));
+    float J[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (N > 0) draw_marks(P, uk, (uint32_t)j, it, N, J);
+    const size_t row = (size_t)j * P.Kpad + k;
+    if (P.jump_channel == 1) {
+      if (N > 0) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) de[i] += J[i];
+      }
+    } else {
+      const float4 rec = P.q > 3 ? make_float4(J[0], J[1], J[2], J[3])
+                                 : make_float4(J[0], J[1], J[2], (float)N);
+      jrec[row] = active ? rec : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    if constexpr (BF16) {
+#pragma unroll
+      for (int i = 0; i < M; ++i) de[i] = __bfloat162float(__float2bfloat16_rn(de[i]));
+    }
+    store_noise<M, BF16>(noise, row, de, active);
+    counts[row] = active ? (uint8_t)N : (uint8_t)0;
+    if (DBG && active) {
+      const size_t rk = (size_t)j * P.K + k;
+      if (dbg_counts) dbg_counts[rk] = (uint8_t)N;
+      if (dbg_J)
+        for (int c = 0; c < P.q; ++c) dbg_J[rk * P.q + c] = J[c];
+    }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Split form, part 2.  rollout_split_kernel: one thread per rollout runs the
+// sequential dynamics from the stored step data.  A register ring of kAhead
+// slots keeps the loads of step j + kAhead in flight while step j is
+// computed (the loop is unrolled by kAhead so every slot index is static);
+// kAhead is the tile's "steps per unrolled chunk".
+// ---------------------------------------------------------------------------
+template <int SYS, bool BF16, int kAhead>
+__global__ void __launch_bounds__(kRolloutThreads)
+rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
+                     const void* __restrict__ noise, const uint8_t* __restrict__ counts,
+                     const float4* __restrict__ jrec, float* __restrict__ s_part,
+                     uint32_t* __restrict__ rho_key) {
+  constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.Kpad) return;  // whole warps: Kpad is a multiple of 32
+  const bool active = k < P.K;
+  const int T = active ? P.T : 0;  // padding lanes skip the loop
+  const bool sj = P.jump_channel == 0;
+  const bool q4 = P.q > 3;
+  float x[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
+  float s = 0.0f, sc = 0.0f;
+
+  float rd[kAhead][m], ru[kAhead][m];
+  float4 rj[kAhead];
+  int rc[kAhead];
+  auto fetch = [&](int slot_unused, int step, float* d, float* u, float4& jr, int& c) {
+    (void)slot_unused;
+    const size_t row = (size_t)step * P.Kpad + k;
+    load_noise<m, BF16>(noise, row, d);
+#pragma unroll
+    for (int i = 0; i < m; ++i) u[i] = __ldg(U + step * m + i);
+    jr = sj ? __ldg(jrec + row) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    c = (sj && q4) ? (int)__ldg(counts + row) : 0;
+  };
+#pragma unroll
+  for (int sl = 0; sl < kAhead; ++sl)
+    if (sl < T) fetch(sl, sl, rd[sl], ru[sl], rj[sl], rc[sl]);
+
+  for (int j0 = 0; j0 < T; j0 += kAhead) {
+#pragma unroll
+    for (int jj = 0; jj < kAhead; ++jj) {
+      const int j = j0 + jj;
+      if (j >= T) break;
+      float de[m], u[m];
+#pragma unroll
+      for (int i = 0; i < m; ++i) {
+        de[i] = rd[jj][i];
+        u[i] = ru[jj][i];
+      }
+      const float J[4] = {rj[jj].x, rj[jj].y, rj[jj].z, rj[jj].w};
+      const bool jumped = sj && (q4 ? rc[jj] > 0 : rj[jj].w > 0.5f);
+      if (j + kAhead < T) fetch(jj, j + kAhead, rd[jj], ru[jj], rj[jj], rc[jj]);
+      cost_and_step<SYS>(P, x, u, de, jumped, J, s, sc);
+    }
+  }
+  finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
 }
 
 // ---------------------------------------------------------------------------
 // Block reductions
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
 __device__ __forceinline__ void warp_sum2(float& s, float& c) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -178,183 +385,265 @@ __device__ __forceinline__ void warp_sum2(float& s, float& c) {
   }
 }
 
-// ---------------------------------------------------------------------------
-// Softmin (Eq. 36-37 with the minimum subtracted): one block of 1024 threads.
-//   rho = min s_k over finite costs; e_k = exp((rho - s_k)/lambda);
-//   Z = sum e_k (compensated); w_k = e_k / Z.
-// diag = {rho + C, Z, (rho + C)/lambda - ln(Z/K)} with C the k-independent
-// cost term.  No finite cost: status = non-finite, weights untouched.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSoftminThreads)
-softmin_kernel(const float* __restrict__ s_part, int K, int Kpad, float inv_lam,
-               const float* __restrict__ cconst, float* __restrict__ w, float* __restrict__ diag,
-               int* __restrict__ status) {
-  __shared__ float red_s[32], red_c[32];
-  __shared__ float sh_rho, sh_Z;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  float mn = INFINITY;
-  for (int k = tid; k < K; k += blockDim.x) mn = fminf(mn, s_part[k]);
-  mn = warp_min(mn);
-  if (lane == 0) red_s[wid] = mn;
+// Compensated sum over the block (kUpdateThreads threads); every thread gets
+// the result.  `sh_s`, `sh_c` hold one pair per warp.
+__device__ __forceinline__ float block_sum2(float s, float c, float* sh_s, float* sh_c) {
+  constexpr int W = kUpdateThreads / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  warp_sum2(s, c);
   __syncthreads();
-  if (wid == 0) {
-    float v = lane < (int)(blockDim.x >> 5) ? red_s[lane] : INFINITY;
-    v = warp_min(v);
-    if (lane == 0) sh_rho = v;
-  }
-  __syncthreads();
-  const float rho = sh_rho;
-  if (!isfinite(rho)) {
-    if (tid == 0) *status = kStatusNonFinite;
-    return;
-  }
-  float zs = 0.0f, zc = 0.0f;
-  for (int k = tid; k < K; k += blockDim.x) two_sum_acc(zs, zc, expf((rho - s_part[k]) * inv_lam));
-  warp_sum2(zs, zc);
   if (lane == 0) {
-    red_s[wid] = zs;
-    red_c[wid] = zc;
+    sh_s[wid] = s;
+    sh_c[wid] = c;
   }
   __syncthreads();
-  if (wid == 0) {
-    float a = lane < (int)(blockDim.x >> 5) ? red_s[lane] : 0.0f;
-    float b = lane < (int)(blockDim.x >> 5) ? red_c[lane] : 0.0f;
-    warp_sum2(a, b);
-    if (lane == 0) sh_Z = a + b;
+  float a = lane < W ? sh_s[lane] : 0.0f;
+  float b = lane < W ? sh_c[lane] : 0.0f;
+  warp_sum2(a, b);
+  return a + b;
+}
+
+// C = sum_j lambda/2 u_j^T Sigma^-1 u_j, the rollout-independent part of S~
+// (Eq. 35), summed with compensation by all threads of the block (every
+// thread gets C).
+template <int M>
+__device__ __forceinline__ float control_cost_sum(const float* __restrict__ U, int T, float lam,
+                                                  const float* inv_sigma2, float* sh_s, float* sh_c) {
+  float s = 0.0f, c = 0.0f;
+  for (int idx = threadIdx.x; idx < T * M; idx += kUpdateThreads) {
+    const float u = U[idx];
+    two_sum_acc(s, c, 0.5f * lam * (u * inv_sigma2[idx % M] * u));
   }
-  __syncthreads();
-  const float Z = sh_Z;
-  for (int k = tid; k < Kpad; k += blockDim.x)
-    w[k] = k < K ? expf((rho - s_part[k]) * inv_lam) / Z : 0.0f;
-  if (tid == 0) {
-    const float rf = rho + *cconst;
-    diag[0] = rf;
-    diag[1] = Z;
-    diag[2] = rf * inv_lam - logf(Z / (float)K);
-  }
+  return block_sum2(s, c, sh_s, sh_c);
+}
+
+// costs[k] = C + S~_k - C, i.e. the full augmented cost of Eq. 34, for the
+// rollout_cost output (each block recomputes C from U).
+template <int M>
+__global__ void __launch_bounds__(kUpdateThreads)
+costs_kernel(const float* __restrict__ U, int T, float lam, float4 inv_sigma2,
+             const float* __restrict__ s_part, int K, float* __restrict__ costs) {
+  __shared__ float sh_s[kUpdateThreads / 32], sh_c[kUpdateThreads / 32];
+  const float is2[4] = {inv_sigma2.x, inv_sigma2.y, inv_sigma2.z, inv_sigma2.w};
+  const float C = control_cost_sum<M>(U, T, lam, is2, sh_s, sh_c);
+  const int k = blockIdx.x * kUpdateThreads + threadIdx.x;
+  if (k < K) costs[k] = C + s_part[k];
 }
 
 // ---------------------------------------------------------------------------
-// Weighted update, split over K.  Block (c, g) owns the rollout chunk c
-// (kUpdateThreads * VPT 16-byte vectors of the step-major noise rows) and the
-// steps g*rows .. g*rows+rows-1.  Each thread keeps the weights of its
-// rollouts in registers across steps, multiplies them into its vectors, and
-// the block reduces the m channel sums with compensated shuffles; the result
-// goes to partial[(c*T + j)*m + i].  Vectors beyond the row are skipped.
+// Weights and update (Eq. 36-37, 49) in one launch, split over K.
+//
+// With rho = min_k S~_k (published by the rollout) the unnormalised weights
+// e_k = exp((rho - S~_k)/lambda) are formed in registers.  Block (c, g) owns
+// the rollout chunk c (kUpdateThreads * VPT 16-byte vectors of each
+// step-major noise row) and the steps g*rows .. g*rows+rows-1 and writes
+//   N_c[j][i] = sum_{k in c} e_k delta_eff[j][k][i]
+// to partial[(c*T + j)*M + i]; blocks of the first step group also write
+// Z_c = sum_{k in c} e_k and the e_k themselves.  The last block to finish
+// (one atomic ticket per block, no waiting) combines the chunks in chunk
+// order: Z = sum_c Z_c, dU = sum_c N_c / Z, U += alpha dU; it then emits u0
+// and shifts the sequence when asked, writes the free-energy diagnostics,
+// advances the iteration counter by it_advance and re-arms the minimum and
+// the ticket.  This is Eq. 37 with the normalisation applied once at the end;
+// every sum is compensated and every order is fixed, so the result does not
+// depend on scheduling.
 // ---------------------------------------------------------------------------
+struct UpdateArgs {
+  const void* noise;
+  const float* s_part;
+  int K, Kpad, T, rows;
+  float inv_lam, lam, alpha;
+  float inv_sigma2[4];
+  float* partial;  // [chunks][T][M]
+  float* zpart;    // [chunks]
+  float* e_out;    // [Kpad]
+  float* U;        // [T][M]
+  float* u0_out;   // [M] or NULL
+  float* diag;     // rho, Z, F
+  int* status;
+  unsigned* done;
+  uint32_t* rho_key;
+  uint32_t* it;
+  uint32_t it_advance;
+  int shift;
+  float u_init[4];
+};
+
 template <bool BF16, int M, int VPT>
-__global__ void __launch_bounds__(kUpdateThreads)
-update_partial_kernel(const void* __restrict__ noise, const float* __restrict__ w, int Kpad, int T,
-                      int rows, float* __restrict__ partial, const int* __restrict__ status) {
+__global__ void __launch_bounds__(kUpdateThreads) update_kernel(const UpdateArgs a) {
   constexpr int E = BF16 ? 8 : 4;  // elements per 16-byte vector
   constexpr int RPV = E / M;       // rollouts per vector
-  __shared__ float red_s[kUpdateThreads / 32][M], red_c[kUpdateThreads / 32][M];
-  if (*status != 0) return;
+  constexpr int W = kUpdateThreads / 32;
+  __shared__ float red_s[W][M], red_c[W][M];
+  __shared__ float sh_s[W], sh_c[W];
+  __shared__ unsigned ticket;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int nvec = Kpad * M / E;  // vectors per row
+  const uint32_t key = *a.rho_key;
+  const bool ok = key < kKeyInf;  // at least one finite cost
+  const float rho = ok ? key_to_float(key) : 0.0f;
+  const int nvec = a.Kpad * M / E;
   const int vbase = blockIdx.x * (kUpdateThreads * VPT) + tid;
-  float wr[VPT][RPV];
-#pragma unroll
-  for (int t = 0; t < VPT; ++t) {
-    const int v = vbase + t * kUpdateThreads;
-#pragma unroll
-    for (int r = 0; r < RPV; ++r) wr[t][r] = v < nvec ? __ldg(w + v * RPV + r) : 0.0f;
-  }
-  const int j_begin = blockIdx.y * rows;
-  const int j_end = min(T, j_begin + rows);
-  const uint4* nv = reinterpret_cast<const uint4*>(noise);
-  for (int j = j_begin; j < j_end; ++j) {
+
+  if (ok) {
+    const int j_begin = blockIdx.y * a.rows;
+    const int j_end = min(a.T, j_begin + a.rows);
+    const uint4* nv = reinterpret_cast<const uint4*>(a.noise);
+    // the first row's loads are issued before the weights are formed
     uint4 buf[VPT];
 #pragma unroll
     for (int t = 0; t < VPT; ++t) {
       const int v = vbase + t * kUpdateThreads;
-      buf[t] = v < nvec ? __ldcs(nv + (size_t)j * nvec + v) : make_uint4(0u, 0u, 0u, 0u);
+      buf[t] = v < nvec && j_begin < j_end ? __ldcs(nv + (size_t)j_begin * nvec + v)
+                                           : make_uint4(0u, 0u, 0u, 0u);
     }
-    float acc[M];
-#pragma unroll
-    for (int i = 0; i < M; ++i) acc[i] = 0.0f;
+    float e[VPT][RPV];
+    float zs = 0.0f, zc = 0.0f;
 #pragma unroll
     for (int t = 0; t < VPT; ++t) {
-      float val[E];
-      if (BF16) {
-        const uint32_t wd[4] = {buf[t].x, buf[t].y, buf[t].z, buf[t].w};
+      const int v = vbase + t * kUpdateThreads;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          val[2 * h] = __uint_as_float(wd[h] << 16);
-          val[2 * h + 1] = __uint_as_float(wd[h] & 0xffff0000u);
+      for (int r = 0; r < RPV; ++r) {
+        const int k = v * RPV + r;
+        e[t][r] = v < nvec ? expf((rho - __ldg(a.s_part + k)) * a.inv_lam) : 0.0f;
+        if (blockIdx.y == 0 && v < nvec) {
+          a.e_out[k] = e[t][r];
+          two_sum_acc(zs, zc, e[t][r]);
         }
-      } else {
-        val[0] = __uint_as_float(buf[t].x);
-        val[1] = __uint_as_float(buf[t].y);
-        val[2] = __uint_as_float(buf[t].z);
-        val[3] = __uint_as_float(buf[t].w);
       }
-#pragma unroll
-      for (int e = 0; e < E; ++e) acc[e % M] = fmaf(wr[t][e / M], val[e], acc[e % M]);
     }
-    float cmp[M];
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      cmp[i] = 0.0f;
-      warp_sum2(acc[i], cmp[i]);
+    if (blockIdx.y == 0) {
+      const float z = block_sum2(zs, zc, sh_s, sh_c);
+      if (tid == 0) a.zpart[blockIdx.x] = z;
     }
-    if (lane == 0) {
+    for (int j = j_begin; j < j_end; ++j) {
+      if (j > j_begin) {
+#pragma unroll
+        for (int t = 0; t < VPT; ++t) {
+          const int v = vbase + t * kUpdateThreads;
+          buf[t] = v < nvec ? __ldcs(nv + (size_t)j * nvec + v) : make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+      float acc[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) acc[i] = 0.0f;
+#pragma unroll
+      for (int t = 0; t < VPT; ++t) {
+        float val[E];
+        if constexpr (BF16) {
+          const uint32_t wd[4] = {buf[t].x, buf[t].y, buf[t].z, buf[t].w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            val[2 * h] = __uint_as_float(wd[h] << 16);
+            val[2 * h + 1] = __uint_as_float(wd[h] & 0xffff0000u);
+          }
+        } else {
+          val[0] = __uint_as_float(buf[t].x);
+          val[1] = __uint_as_float(buf[t].y);
+          val[2] = __uint_as_float(buf[t].z);
+          val[3] = __uint_as_float(buf[t].w);
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q) acc[q % M] = fmaf(e[t][q / M], val[q], acc[q % M]);
+      }
+      float cmp[M];
 #pragma unroll
       for (int i = 0; i < M; ++i) {
-        red_s[wid][i] = acc[i];
-        red_c[wid][i] = cmp[i];
+        cmp[i] = 0.0f;
+        warp_sum2(acc[i], cmp[i]);
       }
-    }
-    __syncthreads();
-    if (wid == 0) {
+      __syncthreads();
+      if (lane == 0) {
 #pragma unroll
-      for (int i = 0; i < M; ++i) {
-        float a = lane < kUpdateThreads / 32 ? red_s[lane][i] : 0.0f;
-        float b = lane < kUpdateThreads / 32 ? red_c[lane][i] : 0.0f;
-        warp_sum2(a, b);
-        if (lane == 0) partial[((size_t)blockIdx.x * T + j) * M + i] = a + b;
+        for (int i = 0; i < M; ++i) {
+          red_s[wid][i] = acc[i];
+          red_c[wid][i] = cmp[i];
+        }
+      }
+      __syncthreads();
+      if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          float s = lane < W ? red_s[lane][i] : 0.0f;
+          float c = lane < W ? red_c[lane][i] : 0.0f;
+          warp_sum2(s, c);
+          if (lane == 0) a.partial[((size_t)blockIdx.x * a.T + j) * M + i] = s + c;
+        }
       }
     }
+  }
+
+  // ---- completion ticket: the last block combines.  The barrier orders the
+  // block's stores before thread 0's fence and ticket; the winner fences
+  // again before reading the other blocks' partials.
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    ticket = atomicAdd(a.done, 1u);
+  }
+  __syncthreads();
+  if (ticket != gridDim.x * gridDim.y - 1) return;
+  __threadfence();
+
+  const int chunks = gridDim.x;
+  const int TM = a.T * M;
+  float Z = 0.0f, C = 0.0f;
+  if (ok) {
+    // the rollout-independent cost of the controls that were rolled out
+    C = control_cost_sum<M>(a.U, a.T, a.lam, a.inv_sigma2, sh_s, sh_c);
+    float zs = 0.0f, zc = 0.0f;
+    for (int c = tid; c < chunks; c += kUpdateThreads) two_sum_acc(zs, zc, __ldcg(a.zpart + c));
+    Z = block_sum2(zs, zc, sh_s, sh_c);
+    const float inv_Z = 1.0f / Z;
+    for (int idx = tid; idx < TM; idx += kUpdateThreads) {
+      float s = 0.0f, c = 0.0f;
+      int ch = 0;
+      for (; ch + 4 <= chunks; ch += 4) {  // four loads in flight
+        float p[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) p[h] = __ldcg(a.partial + (size_t)(ch + h) * TM + idx);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) two_sum_acc(s, c, p[h]);
+      }
+      for (; ch < chunks; ++ch) two_sum_acc(s, c, __ldcg(a.partial + (size_t)ch * TM + idx));
+      const float v = a.U[idx] + a.alpha * ((s + c) * inv_Z);
+      a.U[idx] = v;
+      if (a.shift && a.u0_out && idx < M) a.u0_out[idx] = v;
+    }
     __syncthreads();
+    if (a.shift) {
+      // in-place shift by one step, one block-wide slice at a time
+      for (int base = 0; base < TM; base += kUpdateThreads) {
+        const int idx = base + tid;
+        float v = 0.0f;
+        if (idx < TM) v = idx + M < TM ? a.U[idx + M] : a.u_init[idx - (TM - M)];
+        __syncthreads();
+        if (idx < TM) a.U[idx] = v;
+        __syncthreads();
+      }
+    }
+  } else {
+    if (a.shift && a.u0_out && tid < M) a.u0_out[tid] = a.U[tid];
+  }
+  if (tid == 0) {
+    if (ok) {
+      const float rf = rho + C;
+      a.diag[0] = rf;
+      a.diag[1] = Z;
+      a.diag[2] = rf * a.inv_lam - logf(Z / (float)a.K);
+    } else {
+      *a.status = kStatusNonFinite;
+    }
+    *a.it = *a.it + a.it_advance;
+    *a.rho_key = kKeyEmpty;
+    *a.done = 0u;
   }
 }
 
-// ---------------------------------------------------------------------------
-// Combine the chunk partials in chunk order (compensated), U += alpha * dU,
-// advance the iteration counter, and on the last iteration of an MPC step
-// emit u0 = U_0 and shift (U_i <- U_{i+1}, U_{T-1} <- u_init).  One block;
-// `sh` holds the updated sequence (T*m floats of dynamic shared memory).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCombineThreads)
-update_combine_kernel(const float* __restrict__ partial, int chunks, int T, int m, float alpha,
-                      float* __restrict__ U, const int* __restrict__ status,
-                      uint32_t* __restrict__ it_ptr, int shift, DevProblem P,
-                      float* __restrict__ u0_out) {
-  extern __shared__ float sh[];
-  const int TM = T * m;
-  const bool ok = *status == 0;
-  for (int idx = threadIdx.x; idx < TM; idx += blockDim.x) {
-    float v = U[idx];
-    if (ok) {
-      float s = 0.0f, c = 0.0f;
-      for (int ch = 0; ch < chunks; ++ch) two_sum_acc(s, c, partial[(size_t)ch * TM + idx]);
-      v = v + alpha * (s + c);
-    }
-    sh[idx] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) *it_ptr = *it_ptr + 1u;
-  if (shift && ok) {
-    if (u0_out)
-      for (int i = threadIdx.x; i < m; i += blockDim.x) u0_out[i] = sh[i];
-    for (int idx = threadIdx.x; idx < TM; idx += blockDim.x)
-      U[idx] = idx + m < TM ? sh[idx + m] : P.u_init[idx - (TM - m)];
-  } else {
-    if (shift && u0_out)
-      for (int i = threadIdx.x; i < m; i += blockDim.x) u0_out[i] = sh[i];
-    if (ok)
-      for (int idx = threadIdx.x; idx < TM; idx += blockDim.x) U[idx] = sh[idx];
-  }
+// w_k = e_k / Z for the weights getter.
+__global__ void normalize_weights_kernel(const float* __restrict__ e, const float* __restrict__ diag,
+                                         int K, float* __restrict__ w) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < K) w[k] = e[k] / diag[1];
 }
 
 }  // namespace mj

@@ -76,6 +76,13 @@ class Config(ctypes.Structure):
     ]
 
 
+class Tuning(ctypes.Structure):
+    """mppi_jump_tuning: rollout variant (1 fused, 2 split), threads per block
+    and steps per unrolled chunk."""
+    _fields_ = [("rollout_variant", ctypes.c_int32), ("rollout_block", ctypes.c_int32),
+                ("rollout_chunk", ctypes.c_int32)]
+
+
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
 _st = ctypes.c_int
@@ -110,6 +117,10 @@ _sig("mppi_jump_update", _st, _CTX)
 _sig("mppi_jump_step", _st, _CTX, _P(ctypes.c_float), ctypes.c_int32, _P(ctypes.c_float))
 _sig("mppi_jump_step_async", _st, _CTX, _vp, ctypes.c_int32, _vp)
 _sig("mppi_jump_sync", _st, _CTX)
+_sig("mppi_jump_set_tuning", _st, _CTX, _P(Tuning))
+_sig("mppi_jump_get_tuning", _st, _CTX, _P(Tuning))
+_sig("mppi_jump_autotune", _st, _CTX, _vp, ctypes.c_int32, ctypes.c_int32, _P(Tuning),
+     _P(ctypes.c_float))
 _sig("mppi_jump_enable_timing", _st, _CTX, ctypes.c_int32)
 _sig("mppi_jump_phase_times", _st, _CTX, _P(ctypes.c_float), _P(ctypes.c_int32))
 _sig("mppi_jump_set_debug", _st, _CTX, _vp, _vp)
@@ -212,6 +223,26 @@ def mppi_jump_step_async(ctx, x0_ptr, iters, u0_ptr=0):
 
 def mppi_jump_sync(ctx):
     _check(_lib.mppi_jump_sync(ctx), "sync", ctx)
+
+
+def mppi_jump_set_tuning(ctx, variant, block, chunk=4):
+    t = Tuning(int(variant), int(block), int(chunk))
+    _check(_lib.mppi_jump_set_tuning(ctx, ctypes.byref(t)), "set_tuning", ctx)
+
+
+def mppi_jump_get_tuning(ctx):
+    t = Tuning()
+    _check(_lib.mppi_jump_get_tuning(ctx, ctypes.byref(t)), "get_tuning", ctx)
+    return t.rollout_variant, t.rollout_block, t.rollout_chunk
+
+
+def mppi_jump_autotune(ctx, x0_ptr, iters, reps=5):
+    """Returns ((variant, block, chunk), mean step ms) of the fastest tile."""
+    t = Tuning()
+    ms = ctypes.c_float(0.0)
+    _check(_lib.mppi_jump_autotune(ctx, _vp(x0_ptr), int(iters), int(reps), ctypes.byref(t),
+                                   ctypes.byref(ms)), "autotune", ctx)
+    return (t.rollout_variant, t.rollout_block, t.rollout_chunk), ms.value
 
 
 def mppi_jump_enable_timing(ctx, on=True):
