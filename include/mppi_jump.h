@@ -241,6 +241,62 @@ mppi_status mppi_jump_get_free_energy(mppi_jump_ctx* ctx, float out_host[3]);
 mppi_status mppi_jump_get_state(mppi_jump_ctx* ctx, void* buf_host, size_t* size_host);
 mppi_status mppi_jump_set_state(mppi_jump_ctx* ctx, const void* buf_host, size_t size);
 
+/* ------------------------------------------------------------------------ */
+/* Batched form: n independent MPC instances (any mix of plants, K, T, noise */
+/* laws and iteration counts; one noise dtype for all) advanced together by  */
+/* ONE persistent kernel per batched step, replayed from a CUDA graph.  Each */
+/* instance computes exactly what mppi_jump_step computes for it (Algorithm  */
+/* 1: iters[i] x (rollout_cost + update), then execute u_0 and shift); only  */
+/* the summation order of the weighted update differs.  The kernel claims    */
+/* work items (rollout tiles, weighted-sum chunks, combines) in a fixed      */
+/* dependency order; a dependency wait that exceeds 2 s ends the step with   */
+/* MPPI_ETIMEOUT instead of hanging.                                         */
+/* ------------------------------------------------------------------------ */
+typedef struct mppi_batch mppi_batch;
+
+/* cfgs [n] configurations, iters_host [n] iterations per MPC step (>= 1).
+ * Allocates all device state (cudaMalloc) and sets every U to u_init.
+ * stream: cudaStream_t for all work (NULL: the batch creates its own). */
+mppi_status mppi_batch_create(const mppi_jump_config* cfgs_host, const int32_t* iters_host,
+                              int32_t n, void* stream, mppi_batch** out);
+mppi_status mppi_batch_destroy(mppi_batch* b);
+const char* mppi_batch_last_error(const mppi_batch* b);
+
+/* One batched MPC step.  x0s [n][12] (row i holds instance i's state in its
+ * first n_i entries), u0s [n][4] (first m_i entries).  _async takes device
+ * pointers (u0s may be NULL) and does not synchronise; mppi_batch_step takes
+ * HOST arrays, synchronises and returns the batch status. */
+mppi_status mppi_batch_step_async(mppi_batch* b, const float* x0s, float* u0s);
+mppi_status mppi_batch_step(mppi_batch* b, const float* x0s_host, float* u0s_host);
+/* Synchronises and returns the status word of the last step(s):
+ * MPPI_OK, MPPI_ENONFINITE (an instance had only non-finite costs; its U is
+ * unchanged) or MPPI_ETIMEOUT (a dependency wait expired). */
+mppi_status mppi_batch_sync(mppi_batch* b);
+
+/* Instance i's control sequence [T_i][m_i] (device or host pointer; both
+ * calls synchronise) and iteration counter. */
+mppi_status mppi_batch_get_controls(mppi_batch* b, int32_t i, float* U);
+mppi_status mppi_batch_set_controls(mppi_batch* b, int32_t i, const float* U);
+mppi_status mppi_batch_get_iteration(mppi_batch* b, int32_t i, uint32_t* it_host);
+
+/* Tile: rollouts per block of the persistent kernel (64, 128 or 256). */
+mppi_status mppi_batch_set_tuning(mppi_batch* b, int32_t block);
+mppi_status mppi_batch_get_tuning(mppi_batch* b, int32_t* block_host);
+/* Failure-path test hook: with on != 0 the following steps start with a work
+ * item whose dependency is never satisfied, so the step ends with
+ * MPPI_ETIMEOUT after the bounded wait (about 2 s) instead of running; the
+ * instances' controls may then be partially advanced.  on = 0 restores the
+ * normal work list. */
+mppi_status mppi_batch_inject_stall(mppi_batch* b, int32_t on);
+/* Autotuner: times `reps` batched steps per block size from device x0s and
+ * keeps the fastest; controls and counters are restored afterwards. */
+mppi_status mppi_batch_autotune(mppi_batch* b, const float* x0s, int32_t reps,
+                                int32_t* best_block_host, float* best_ms_host);
+/* Trajectory-steps of one batched step (sum of K_i T_i iters_i), the number of
+ * work items and the persistent grid size (any may be NULL). */
+mppi_status mppi_batch_info(mppi_batch* b, int64_t* steps_per_solve_host, int32_t* n_items_host,
+                            int32_t* grid_host);
+
 #ifdef __cplusplus
 }
 #endif

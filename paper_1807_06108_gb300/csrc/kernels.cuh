@@ -181,6 +181,12 @@ __device__ __forceinline__ void finish_rollout(const DevProblem& P, int k, bool 
 // so each warp store is contiguous.  Rollouts K..Kpad-1 (padding) store zero
 // noise and an infinite cost.
 // ---------------------------------------------------------------------------
+template <int SYS, bool BF16, bool DBG, bool COHERENT>
+__device__ __forceinline__ void fused_rollout_thread(
+    const DevProblem& P, const float* __restrict__ x0, const float* __restrict__ U, uint32_t it, int k,
+    float* __restrict__ s_part, void* __restrict__ noise, uint32_t* __restrict__ rho_key,
+    uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J);
+
 template <int SYS, bool BF16, bool DBG>
 __global__ void __launch_bounds__(kRolloutThreads)
 rollout_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
@@ -188,15 +194,27 @@ rollout_kernel(const DevProblem P, const float* __restrict__ x0, const float* __
                void* __restrict__ noise,
                uint32_t* __restrict__ rho_key, uint8_t* __restrict__ dbg_counts,
                float* __restrict__ dbg_J) {
-  constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P.Kpad) return;
+  fused_rollout_thread<SYS, BF16, DBG, false>(P, x0, U, __ldg(it_ptr) + it_off, k, s_part, noise,
+                                              rho_key, dbg_counts, dbg_J);
+}
+
+// The body of the fused rollout for rollout k < Kpad of a problem; every lane
+// of the warp must run it (k >= Kpad lanes are not allowed: Kpad is a
+// multiple of 32).  COHERENT reads x0 and U through L2, for callers in which
+// another block of the same launch may have written them.
+template <int SYS, bool BF16, bool DBG, bool COHERENT>
+__device__ __forceinline__ void fused_rollout_thread(
+    const DevProblem& P, const float* __restrict__ x0, const float* __restrict__ U, uint32_t it, int k,
+    float* __restrict__ s_part, void* __restrict__ noise, uint32_t* __restrict__ rho_key,
+    uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J) {
+  constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
   const bool active = k < P.K;
-  const uint32_t it = __ldg(it_ptr) + it_off;
   const uint32_t uk = (uint32_t)k;
   float x[n];
 #pragma unroll
-  for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
+  for (int i = 0; i < n; ++i) x[i] = COHERENT ? __ldcg(x0 + i) : __ldg(x0 + i);
   float s = 0.0f, sc = 0.0f;
   for (int j0 = 0; j0 < P.T; j0 += 4) {
     const uint4 wcount = philox4x32_10(uk, (uint32_t)(j0 >> 2), it, 1u, P.key0, P.key1);
@@ -230,7 +248,7 @@ rollout_kernel(const DevProblem P, const float* __restrict__ x0, const float* __
       }
       float u[m];
 #pragma unroll
-      for (int i = 0; i < m; ++i) u[i] = __ldg(U + j * m + i);
+      for (int i = 0; i < m; ++i) u[i] = COHERENT ? __ldcg(U + j * m + i) : __ldg(U + j * m + i);
       cost_and_step<SYS>(P, x, u, de, N > 0, J, s, sc);
       store_noise<m, BF16>(noise, (size_t)j * P.Kpad + k, de, active);
       if (DBG && active) {
@@ -374,7 +392,7 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
 }
 
 // ---------------------------------------------------------------------------
-// Block reductions
+// Block reductions (NT threads per block)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void warp_sum2(float& s, float& c) {
 #pragma unroll
@@ -385,10 +403,18 @@ __device__ __forceinline__ void warp_sum2(float& s, float& c) {
   }
 }
 
-// Compensated sum over the block (kUpdateThreads threads); every thread gets
-// the result.  `sh_s`, `sh_c` hold one pair per warp.
+// Shared scratch of the update bodies for NT threads and M channels.
+template <int NT, int M>
+struct UpdateShared {
+  float red_s[NT / 32][M], red_c[NT / 32][M];
+  float sh_s[NT / 32], sh_c[NT / 32];
+  unsigned ticket;
+};
+
+// Compensated sum over the block; every thread gets the result.
+template <int NT>
 __device__ __forceinline__ float block_sum2(float s, float c, float* sh_s, float* sh_c) {
-  constexpr int W = kUpdateThreads / 32;
+  constexpr int W = NT / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   warp_sum2(s, c);
   __syncthreads();
@@ -404,20 +430,21 @@ __device__ __forceinline__ float block_sum2(float s, float c, float* sh_s, float
 }
 
 // C = sum_j lambda/2 u_j^T Sigma^-1 u_j, the rollout-independent part of S~
-// (Eq. 35), summed with compensation by all threads of the block (every
-// thread gets C).
-template <int M>
+// (Eq. 35), summed with compensation by the whole block (every thread gets C).
+// U is read through L2 (it may have been written by another block of the
+// same launch).
+template <int M, int NT>
 __device__ __forceinline__ float control_cost_sum(const float* __restrict__ U, int T, float lam,
                                                   const float* inv_sigma2, float* sh_s, float* sh_c) {
   float s = 0.0f, c = 0.0f;
-  for (int idx = threadIdx.x; idx < T * M; idx += kUpdateThreads) {
-    const float u = U[idx];
+  for (int idx = threadIdx.x; idx < T * M; idx += NT) {
+    const float u = __ldcg(U + idx);
     two_sum_acc(s, c, 0.5f * lam * (u * inv_sigma2[idx % M] * u));
   }
-  return block_sum2(s, c, sh_s, sh_c);
+  return block_sum2<NT>(s, c, sh_s, sh_c);
 }
 
-// costs[k] = C + S~_k - C, i.e. the full augmented cost of Eq. 34, for the
+// costs[k] = C + (S~_k - C), the full augmented cost of Eq. 34, for the
 // rollout_cost output (each block recomputes C from U).
 template <int M>
 __global__ void __launch_bounds__(kUpdateThreads)
@@ -425,28 +452,28 @@ costs_kernel(const float* __restrict__ U, int T, float lam, float4 inv_sigma2,
              const float* __restrict__ s_part, int K, float* __restrict__ costs) {
   __shared__ float sh_s[kUpdateThreads / 32], sh_c[kUpdateThreads / 32];
   const float is2[4] = {inv_sigma2.x, inv_sigma2.y, inv_sigma2.z, inv_sigma2.w};
-  const float C = control_cost_sum<M>(U, T, lam, is2, sh_s, sh_c);
+  const float C = control_cost_sum<M, kUpdateThreads>(U, T, lam, is2, sh_s, sh_c);
   const int k = blockIdx.x * kUpdateThreads + threadIdx.x;
   if (k < K) costs[k] = C + s_part[k];
 }
 
 // ---------------------------------------------------------------------------
-// Weights and update (Eq. 36-37, 49) in one launch, split over K.
+// Weights and update (Eq. 36-37, 49), split over K.
 //
 // With rho = min_k S~_k (published by the rollout) the unnormalised weights
-// e_k = exp((rho - S~_k)/lambda) are formed in registers.  Block (c, g) owns
-// the rollout chunk c (kUpdateThreads * VPT 16-byte vectors of each
-// step-major noise row) and the steps g*rows .. g*rows+rows-1 and writes
+// e_k = exp((rho - S~_k)/lambda) are formed in registers.  The partial body
+// of chunk c (NT * VPT 16-byte vectors of each step-major noise row) and
+// steps j_begin .. j_end-1 writes
 //   N_c[j][i] = sum_{k in c} e_k delta_eff[j][k][i]
-// to partial[(c*T + j)*M + i]; blocks of the first step group also write
-// Z_c = sum_{k in c} e_k and the e_k themselves.  The last block to finish
-// (one atomic ticket per block, no waiting) combines the chunks in chunk
-// order: Z = sum_c Z_c, dU = sum_c N_c / Z, U += alpha dU; it then emits u0
-// and shifts the sequence when asked, writes the free-energy diagnostics,
-// advances the iteration counter by it_advance and re-arms the minimum and
-// the ticket.  This is Eq. 37 with the normalisation applied once at the end;
-// every sum is compensated and every order is fixed, so the result does not
-// depend on scheduling.
+// to partial[(c*T + j)*M + i]; the block that owns the first steps of a
+// chunk also writes Z_c = sum_{k in c} e_k and the e_k themselves.  The
+// combine body sums the chunks in chunk order: Z = sum_c Z_c,
+// dU = sum_c N_c / Z, U += alpha dU; it then emits u0 and shifts the sequence
+// when asked, writes the free-energy diagnostics, advances the iteration
+// counter and re-arms the running minimum.  This is Eq. 37 with the
+// normalisation applied once at the end; every sum is compensated and every
+// order fixed, so the result does not depend on scheduling.  Data that other
+// blocks of the same launch wrote is read through L2 (ld.global.cg).
 // ---------------------------------------------------------------------------
 struct UpdateArgs {
   const void* noise;
@@ -469,160 +496,149 @@ struct UpdateArgs {
   float u_init[4];
 };
 
-template <bool BF16, int M, int VPT>
-__global__ void __launch_bounds__(kUpdateThreads) update_kernel(const UpdateArgs a) {
+template <bool BF16, int M, int VPT, int NT>
+__device__ __forceinline__ void update_partial_body(const UpdateArgs& a, float rho, int chunk,
+                                                    int j_begin, int j_end, bool write_z,
+                                                    UpdateShared<NT, M>& sh) {
   constexpr int E = BF16 ? 8 : 4;  // elements per 16-byte vector
   constexpr int RPV = E / M;       // rollouts per vector
-  constexpr int W = kUpdateThreads / 32;
-  __shared__ float red_s[W][M], red_c[W][M];
-  __shared__ float sh_s[W], sh_c[W];
-  __shared__ unsigned ticket;
+  constexpr int W = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint32_t key = *a.rho_key;
-  const bool ok = key < kKeyInf;  // at least one finite cost
-  const float rho = ok ? key_to_float(key) : 0.0f;
   const int nvec = a.Kpad * M / E;
-  const int vbase = blockIdx.x * (kUpdateThreads * VPT) + tid;
-
-  if (ok) {
-    const int j_begin = blockIdx.y * a.rows;
-    const int j_end = min(a.T, j_begin + a.rows);
-    const uint4* nv = reinterpret_cast<const uint4*>(a.noise);
-    // the first row's loads are issued before the weights are formed
-    uint4 buf[VPT];
+  const int vbase = chunk * (NT * VPT) + tid;
+  const uint4* nv = reinterpret_cast<const uint4*>(a.noise);
+  // the first row's loads are issued before the weights are formed
+  uint4 buf[VPT];
 #pragma unroll
-    for (int t = 0; t < VPT; ++t) {
-      const int v = vbase + t * kUpdateThreads;
-      buf[t] = v < nvec && j_begin < j_end ? __ldcs(nv + (size_t)j_begin * nvec + v)
-                                           : make_uint4(0u, 0u, 0u, 0u);
-    }
-    float e[VPT][RPV];
-    float zs = 0.0f, zc = 0.0f;
+  for (int t = 0; t < VPT; ++t) {
+    const int v = vbase + t * NT;
+    buf[t] = v < nvec && j_begin < j_end ? __ldcg(nv + (size_t)j_begin * nvec + v)
+                                         : make_uint4(0u, 0u, 0u, 0u);
+  }
+  float e[VPT][RPV];
+  float zs = 0.0f, zc = 0.0f;
 #pragma unroll
-    for (int t = 0; t < VPT; ++t) {
-      const int v = vbase + t * kUpdateThreads;
+  for (int t = 0; t < VPT; ++t) {
+    const int v = vbase + t * NT;
 #pragma unroll
-      for (int r = 0; r < RPV; ++r) {
-        const int k = v * RPV + r;
-        e[t][r] = v < nvec ? expf((rho - __ldg(a.s_part + k)) * a.inv_lam) : 0.0f;
-        if (blockIdx.y == 0 && v < nvec) {
-          a.e_out[k] = e[t][r];
-          two_sum_acc(zs, zc, e[t][r]);
-        }
+    for (int r = 0; r < RPV; ++r) {
+      const int k = v * RPV + r;
+      e[t][r] = v < nvec ? expf((rho - __ldcg(a.s_part + k)) * a.inv_lam) : 0.0f;
+      if (write_z && v < nvec) {
+        a.e_out[k] = e[t][r];
+        two_sum_acc(zs, zc, e[t][r]);
       }
     }
-    if (blockIdx.y == 0) {
-      const float z = block_sum2(zs, zc, sh_s, sh_c);
-      if (tid == 0) a.zpart[blockIdx.x] = z;
-    }
-    for (int j = j_begin; j < j_end; ++j) {
-      if (j > j_begin) {
-#pragma unroll
-        for (int t = 0; t < VPT; ++t) {
-          const int v = vbase + t * kUpdateThreads;
-          buf[t] = v < nvec ? __ldcs(nv + (size_t)j * nvec + v) : make_uint4(0u, 0u, 0u, 0u);
-        }
-      }
-      float acc[M];
-#pragma unroll
-      for (int i = 0; i < M; ++i) acc[i] = 0.0f;
+  }
+  if (write_z) {
+    const float z = block_sum2<NT>(zs, zc, sh.sh_s, sh.sh_c);
+    if (tid == 0) a.zpart[chunk] = z;
+  }
+  for (int j = j_begin; j < j_end; ++j) {
+    if (j > j_begin) {
 #pragma unroll
       for (int t = 0; t < VPT; ++t) {
-        float val[E];
-        if constexpr (BF16) {
-          const uint32_t wd[4] = {buf[t].x, buf[t].y, buf[t].z, buf[t].w};
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            val[2 * h] = __uint_as_float(wd[h] << 16);
-            val[2 * h + 1] = __uint_as_float(wd[h] & 0xffff0000u);
-          }
-        } else {
-          val[0] = __uint_as_float(buf[t].x);
-          val[1] = __uint_as_float(buf[t].y);
-          val[2] = __uint_as_float(buf[t].z);
-          val[3] = __uint_as_float(buf[t].w);
-        }
-#pragma unroll
-        for (int q = 0; q < E; ++q) acc[q % M] = fmaf(e[t][q / M], val[q], acc[q % M]);
+        const int v = vbase + t * NT;
+        buf[t] = v < nvec ? __ldcg(nv + (size_t)j * nvec + v) : make_uint4(0u, 0u, 0u, 0u);
       }
-      float cmp[M];
+    }
+    float acc[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) acc[i] = 0.0f;
+#pragma unroll
+    for (int t = 0; t < VPT; ++t) {
+      float val[E];
+      if constexpr (BF16) {
+        const uint32_t wd[4] = {buf[t].x, buf[t].y, buf[t].z, buf[t].w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          val[2 * h] = __uint_as_float(wd[h] << 16);
+          val[2 * h + 1] = __uint_as_float(wd[h] & 0xffff0000u);
+        }
+      } else {
+        val[0] = __uint_as_float(buf[t].x);
+        val[1] = __uint_as_float(buf[t].y);
+        val[2] = __uint_as_float(buf[t].z);
+        val[3] = __uint_as_float(buf[t].w);
+      }
+#pragma unroll
+      for (int q = 0; q < E; ++q) acc[q % M] = fmaf(e[t][q / M], val[q], acc[q % M]);
+    }
+    float cmp[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      cmp[i] = 0.0f;
+      warp_sum2(acc[i], cmp[i]);
+    }
+    __syncthreads();
+    if (lane == 0) {
 #pragma unroll
       for (int i = 0; i < M; ++i) {
-        cmp[i] = 0.0f;
-        warp_sum2(acc[i], cmp[i]);
+        sh.red_s[wid][i] = acc[i];
+        sh.red_c[wid][i] = cmp[i];
       }
-      __syncthreads();
-      if (lane == 0) {
+    }
+    __syncthreads();
+    if (wid == 0) {
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-          red_s[wid][i] = acc[i];
-          red_c[wid][i] = cmp[i];
-        }
-      }
-      __syncthreads();
-      if (wid == 0) {
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-          float s = lane < W ? red_s[lane][i] : 0.0f;
-          float c = lane < W ? red_c[lane][i] : 0.0f;
-          warp_sum2(s, c);
-          if (lane == 0) a.partial[((size_t)blockIdx.x * a.T + j) * M + i] = s + c;
-        }
+      for (int i = 0; i < M; ++i) {
+        float s = lane < W ? sh.red_s[lane][i] : 0.0f;
+        float c = lane < W ? sh.red_c[lane][i] : 0.0f;
+        warp_sum2(s, c);
+        if (lane == 0) a.partial[((size_t)chunk * a.T + j) * M + i] = s + c;
       }
     }
   }
+}
 
-  // ---- completion ticket: the last block combines.  The barrier orders the
-  // block's stores before thread 0's fence and ticket; the winner fences
-  // again before reading the other blocks' partials.
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    ticket = atomicAdd(a.done, 1u);
-  }
-  __syncthreads();
-  if (ticket != gridDim.x * gridDim.y - 1) return;
-  __threadfence();
-
-  const int chunks = gridDim.x;
+template <int M, int NT>
+__device__ __forceinline__ void update_combine_body(const UpdateArgs& a, bool ok, float rho,
+                                                    int chunks, UpdateShared<NT, M>& sh) {
+  const int tid = threadIdx.x;
   const int TM = a.T * M;
   float Z = 0.0f, C = 0.0f;
   if (ok) {
     // the rollout-independent cost of the controls that were rolled out
-    C = control_cost_sum<M>(a.U, a.T, a.lam, a.inv_sigma2, sh_s, sh_c);
+    C = control_cost_sum<M, NT>(a.U, a.T, a.lam, a.inv_sigma2, sh.sh_s, sh.sh_c);
     float zs = 0.0f, zc = 0.0f;
-    for (int c = tid; c < chunks; c += kUpdateThreads) two_sum_acc(zs, zc, __ldcg(a.zpart + c));
-    Z = block_sum2(zs, zc, sh_s, sh_c);
+    for (int c = tid; c < chunks; c += NT) two_sum_acc(zs, zc, __ldcg(a.zpart + c));
+    Z = block_sum2<NT>(zs, zc, sh.sh_s, sh.sh_c);
     const float inv_Z = 1.0f / Z;
-    for (int idx = tid; idx < TM; idx += kUpdateThreads) {
-      float s = 0.0f, c = 0.0f;
-      int ch = 0;
-      for (; ch + 4 <= chunks; ch += 4) {  // four loads in flight
-        float p[4];
+    // One block-wide slice at a time: every thread reads its old U entry and
+    // forms the updated value; with the MPC shift, the value is written one
+    // step earlier (entry idx - M; the first step's value is u0) after a
+    // barrier, so no thread overwrites an entry another thread has yet to
+    // read, and no entry written here is read back.
+    for (int base = 0; base < TM; base += NT) {
+      const int idx = base + tid;
+      float v = 0.0f;
+      if (idx < TM) {
+        float s = 0.0f, c = 0.0f;
+        int ch = 0;
+        for (; ch + 4 <= chunks; ch += 4) {  // four loads in flight
+          float p[4];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) p[h] = __ldcg(a.partial + (size_t)(ch + h) * TM + idx);
+          for (int h = 0; h < 4; ++h) p[h] = __ldcg(a.partial + (size_t)(ch + h) * TM + idx);
 #pragma unroll
-        for (int h = 0; h < 4; ++h) two_sum_acc(s, c, p[h]);
+          for (int h = 0; h < 4; ++h) two_sum_acc(s, c, p[h]);
+        }
+        for (; ch < chunks; ++ch) two_sum_acc(s, c, __ldcg(a.partial + (size_t)ch * TM + idx));
+        v = __ldcg(a.U + idx) + a.alpha * ((s + c) * inv_Z);
       }
-      for (; ch < chunks; ++ch) two_sum_acc(s, c, __ldcg(a.partial + (size_t)ch * TM + idx));
-      const float v = a.U[idx] + a.alpha * ((s + c) * inv_Z);
-      a.U[idx] = v;
-      if (a.shift && a.u0_out && idx < M) a.u0_out[idx] = v;
-    }
-    __syncthreads();
-    if (a.shift) {
-      // in-place shift by one step, one block-wide slice at a time
-      for (int base = 0; base < TM; base += kUpdateThreads) {
-        const int idx = base + tid;
-        float v = 0.0f;
-        if (idx < TM) v = idx + M < TM ? a.U[idx + M] : a.u_init[idx - (TM - M)];
+      if (a.shift) {
         __syncthreads();
-        if (idx < TM) a.U[idx] = v;
+        if (idx < TM) {
+          if (idx >= M) a.U[idx - M] = v;
+          else if (a.u0_out) a.u0_out[idx] = v;
+          if (idx >= TM - M) a.U[idx] = a.u_init[idx - (TM - M)];
+        }
         __syncthreads();
+      } else if (idx < TM) {
+        a.U[idx] = v;
       }
     }
   } else {
-    if (a.shift && a.u0_out && tid < M) a.u0_out[tid] = a.U[tid];
+    if (a.shift && a.u0_out && tid < M) a.u0_out[tid] = __ldcg(a.U + tid);
   }
   if (tid == 0) {
     if (ok) {
@@ -635,12 +651,40 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const UpdateArgs
     }
     *a.it = *a.it + a.it_advance;
     *a.rho_key = kKeyEmpty;
-    *a.done = 0u;
   }
 }
 
+// One launch: block (c, g) runs the partial body for chunk c and steps
+// g*rows .., then takes a completion ticket (one atomic per block, no
+// waiting); the last block runs the combine body and re-arms the ticket.
+template <bool BF16, int M, int VPT>
+__global__ void __launch_bounds__(kUpdateThreads) update_kernel(const UpdateArgs a) {
+  __shared__ UpdateShared<kUpdateThreads, M> sh;
+  const uint32_t key = __ldcg(a.rho_key);
+  const bool ok = key < kKeyInf;  // at least one finite cost
+  const float rho = ok ? key_to_float(key) : 0.0f;
+  if (ok) {
+    const int j_begin = blockIdx.y * a.rows;
+    const int j_end = min(a.T, j_begin + a.rows);
+    update_partial_body<BF16, M, VPT, kUpdateThreads>(a, rho, blockIdx.x, j_begin, j_end,
+                                                      blockIdx.y == 0, sh);
+  }
+  // the barrier orders the block's stores before thread 0's fence and
+  // ticket; the winner fences again before reading the other partials
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    sh.ticket = atomicAdd(a.done, 1u);
+  }
+  __syncthreads();
+  if (sh.ticket != gridDim.x * gridDim.y - 1) return;
+  __threadfence();
+  update_combine_body<M, kUpdateThreads>(a, ok, rho, gridDim.x, sh);
+  if (threadIdx.x == 0) *a.done = 0u;
+}
+
 // w_k = e_k / Z for the weights getter.
-__global__ void normalize_weights_kernel(const float* __restrict__ e, const float* __restrict__ diag,
+static __global__ void normalize_weights_kernel(const float* __restrict__ e, const float* __restrict__ diag,
                                          int K, float* __restrict__ w) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < K) w[k] = e[k] / diag[1];

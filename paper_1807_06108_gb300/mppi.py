@@ -461,3 +461,133 @@ class Solver:
 
     def set_state(self, blob):
         mppi_jump_set_state(self.ctx, blob)
+
+
+# --------------------------------------------------------------------------
+# Batched form
+# --------------------------------------------------------------------------
+
+_sig("mppi_batch_create", _st, _P(Config), _P(ctypes.c_int32), ctypes.c_int32, _vp, _P(_vp))
+_sig("mppi_batch_destroy", _st, _vp)
+_sig("mppi_batch_last_error", ctypes.c_char_p, _vp)
+_sig("mppi_batch_step_async", _st, _vp, _vp, _vp)
+_sig("mppi_batch_step", _st, _vp, _P(ctypes.c_float), _P(ctypes.c_float))
+_sig("mppi_batch_sync", _st, _vp)
+_sig("mppi_batch_get_controls", _st, _vp, ctypes.c_int32, _vp)
+_sig("mppi_batch_set_controls", _st, _vp, ctypes.c_int32, _vp)
+_sig("mppi_batch_get_iteration", _st, _vp, ctypes.c_int32, _P(ctypes.c_uint32))
+_sig("mppi_batch_set_tuning", _st, _vp, ctypes.c_int32)
+_sig("mppi_batch_get_tuning", _st, _vp, _P(ctypes.c_int32))
+_sig("mppi_batch_autotune", _st, _vp, _vp, ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_float))
+_sig("mppi_batch_info", _st, _vp, _P(ctypes.c_int64), _P(ctypes.c_int32), _P(ctypes.c_int32))
+_sig("mppi_batch_inject_stall", _st, _vp, ctypes.c_int32)
+
+STATE_STRIDE = 12
+CONTROL_STRIDE = 4
+
+
+def _bcheck(st, what, b=None):
+    if st != OK:
+        detail = (_lib.mppi_batch_last_error(b) or b"").decode(errors="replace") if b else ""
+        raise MppiError(st, what, detail)
+
+
+class Batch:
+    """n independent MPC problems advanced by one persistent launch per step."""
+
+    def __init__(self, probs, stream=None):
+        import torch
+        self.torch = torch
+        self.probs = list(probs)
+        self.n = len(self.probs)
+        cfgs = (Config * self.n)(*[config_from_problem(p) for p in self.probs])
+        iters = (ctypes.c_int32 * self.n)(*[p["iters"] for p in self.probs])
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.handle = _vp()
+        _bcheck(_lib.mppi_batch_create(cfgs, iters, self.n, _vp(self.stream.cuda_stream),
+                                       ctypes.byref(self.handle)), "batch_create")
+        with torch.cuda.stream(self.stream):
+            self.x0s = torch.zeros((self.n, STATE_STRIDE), dtype=torch.float32, device="cuda")
+            self.u0s = torch.zeros((self.n, CONTROL_STRIDE), dtype=torch.float32, device="cuda")
+        self.stream.synchronize()
+
+    def close(self):
+        if self.handle:
+            _lib.mppi_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        s, n, g = ctypes.c_int64(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        _bcheck(_lib.mppi_batch_info(self.handle, ctypes.byref(s), ctypes.byref(n), ctypes.byref(g)),
+                "batch_info", self.handle)
+        return {"steps_per_solve": s.value, "items": n.value, "grid": g.value}
+
+    def pack_states(self, states):
+        x = np.zeros((self.n, STATE_STRIDE), dtype=np.float32)
+        for i, s in enumerate(states):
+            s = np.asarray(s, dtype=np.float32)
+            x[i, :s.shape[0]] = s
+        return x
+
+    def set_states(self, states):
+        x = self.torch.from_numpy(self.pack_states(states))
+        with self.torch.cuda.stream(self.stream):
+            self.x0s.copy_(x)
+        self.stream.synchronize()
+
+    def step(self, states):
+        """Synchronous batched step from host states; returns u0 per instance."""
+        x = np.ascontiguousarray(self.pack_states(states))
+        u = np.zeros((self.n, CONTROL_STRIDE), dtype=np.float32)
+        _bcheck(_lib.mppi_batch_step(self.handle, x.ctypes.data_as(_P(ctypes.c_float)),
+                                     u.ctypes.data_as(_P(ctypes.c_float))), "batch_step", self.handle)
+        return [u[i, :_wl.CONTROL_DIM[p["system"]]] for i, p in enumerate(self.probs)]
+
+    def step_async(self):
+        _bcheck(_lib.mppi_batch_step_async(self.handle, _vp(self.x0s.data_ptr()),
+                                           _vp(self.u0s.data_ptr())), "batch_step_async", self.handle)
+
+    def sync(self):
+        _bcheck(_lib.mppi_batch_sync(self.handle), "batch_sync", self.handle)
+
+    def controls(self, i):
+        p = self.probs[i]
+        U = np.zeros((p["T"], _wl.CONTROL_DIM[p["system"]]), dtype=np.float32)
+        _bcheck(_lib.mppi_batch_get_controls(self.handle, i, _vp(U.ctypes.data)), "batch_get_controls",
+                self.handle)
+        return U
+
+    def set_controls(self, i, U):
+        U = np.ascontiguousarray(U, dtype=np.float32)
+        _bcheck(_lib.mppi_batch_set_controls(self.handle, i, _vp(U.ctypes.data)), "batch_set_controls",
+                self.handle)
+
+    def iteration(self, i):
+        v = ctypes.c_uint32(0)
+        _bcheck(_lib.mppi_batch_get_iteration(self.handle, i, ctypes.byref(v)), "batch_get_iteration",
+                self.handle)
+        return v.value
+
+    def set_tuning(self, block):
+        _bcheck(_lib.mppi_batch_set_tuning(self.handle, int(block)), "batch_set_tuning", self.handle)
+
+    def tuning(self):
+        v = ctypes.c_int32(0)
+        _bcheck(_lib.mppi_batch_get_tuning(self.handle, ctypes.byref(v)), "batch_get_tuning", self.handle)
+        return v.value
+
+    def autotune(self, reps=3):
+        blk, ms = ctypes.c_int32(0), ctypes.c_float(0.0)
+        _bcheck(_lib.mppi_batch_autotune(self.handle, _vp(self.x0s.data_ptr()), int(reps),
+                                         ctypes.byref(blk), ctypes.byref(ms)), "batch_autotune", self.handle)
+        return blk.value, ms.value
+
+    def inject_stall(self, on=True):
+        _bcheck(_lib.mppi_batch_inject_stall(self.handle, int(bool(on))), "batch_inject_stall",
+                self.handle)

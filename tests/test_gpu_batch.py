@@ -1,0 +1,113 @@
+"""GPU tests of the batched form: one persistent launch per batched step
+solves every instance as Algorithm 1 would on its own (checked against the
+oracle's MPC step, instance by instance, over two consecutive steps), any
+block size gives the same answer within the update tolerance, the
+autotuner leaves the state untouched, and a dependency wait that never
+completes ends the step with MPPI_ETIMEOUT instead of hanging."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_06108_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed(noise_dtype):
+    return [
+        W.cartpole_k1000(K=300, T=17, seed=11, noise_dtype=noise_dtype, iters=1),
+        W.quadrotor_k4096(K=700, T=40, seed=12, noise_dtype=noise_dtype, iters=3, lam=20.0),
+        W.cartpole_k1000(K=1000, T=50, seed=13, noise_dtype=noise_dtype, iters=2, nu=3.0),
+        W.quadrotor_k4096(K=2048, T=23, seed=14, noise_dtype=noise_dtype, iters=1, lam=50.0,
+                          mark_law="laplace", nu=4.0),
+        W.quadrotor_k4096(K=96, T=64, seed=15, noise_dtype=noise_dtype, iters=2,
+                          jump_channel="control", mark_scale=0.3, lam=30.0),
+        W.cartpole_k1000(K=33, T=5, seed=16, noise_dtype=noise_dtype, iters=4),
+    ]
+
+
+def _states(probs, rng):
+    return [W.random_state(p, rng, 0.1) for p in probs]
+
+
+def _check_against_oracle(probs, states, U_in, it0, u0s, U_out):
+    for i, p in enumerate(probs):
+        u0_ref, U_ref = oracle.step(p, states[i], U_in[i], it0[i], p["iters"])
+        U0 = np.asarray(U_in[i], dtype=np.float64)
+        den = max(np.max(np.abs(U_ref[:-1] - U0[1:])), np.max(np.abs(u0_ref - U0[0])), 1e-30)
+        err = max(np.max(np.abs(U_out[i][:-1] - U_ref[:-1])), np.max(np.abs(u0s[i] - u0_ref))) / den
+        np.testing.assert_array_equal(U_out[i][-1], np.asarray(p["u_init"], dtype=np.float32))
+        assert err <= 1e-4 * p["iters"], (p["name"], err)
+
+
+@pytest.mark.parametrize("noise_dtype", ["bf16", "f32"])
+def test_batched_steps_match_oracle(cuda, noise_dtype):
+    from paper_1807_06108_gb300 import mppi
+    probs = _mixed(noise_dtype)
+    rng = np.random.default_rng(0)
+    b = mppi.Batch(probs)
+    try:
+        its = [0] * len(probs)
+        U_in = [W.initial_controls(p) for p in probs]
+        for _ in range(2):
+            states = _states(probs, rng)
+            u0s = b.step(states)
+            U_out = [b.controls(i) for i in range(len(probs))]
+            _check_against_oracle(probs, states, U_in, its, u0s, U_out)
+            its = [its[i] + p["iters"] for i, p in enumerate(probs)]
+            assert [b.iteration(i) for i in range(len(probs))] == its
+            U_in = U_out
+    finally:
+        b.close()
+
+
+def test_block_sizes_agree_and_autotune_restores(cuda):
+    from paper_1807_06108_gb300 import mppi
+    probs = _mixed("bf16")
+    states = _states(probs, np.random.default_rng(1))
+    results = {}
+    for block in (64, 128, 256):
+        b = mppi.Batch(probs)
+        try:
+            b.set_tuning(block)
+            assert b.tuning() == block
+            b.step(states)
+            results[block] = [b.controls(i) for i in range(len(probs))]
+        finally:
+            b.close()
+    for block in (64, 256):
+        for i in range(len(probs)):
+            ref = results[128][i].astype(np.float64)
+            den = max(np.max(np.abs(ref - W.initial_controls(probs[i]))), 1e-30)
+            assert np.max(np.abs(results[block][i] - ref)) / den <= 1e-4 * probs[i]["iters"]
+    b = mppi.Batch(probs)
+    try:
+        b.set_states(states)
+        blk, ms = b.autotune(reps=1)
+        assert blk in (64, 128, 256) and ms > 0
+        assert all(b.iteration(i) == 0 for i in range(len(probs)))
+        b.set_tuning(128)
+        b.step(states)
+        for i in range(len(probs)):
+            np.testing.assert_array_equal(b.controls(i), results[128][i])
+    finally:
+        b.close()
+
+
+def test_stalled_dependency_times_out_and_recovers(cuda):
+    from paper_1807_06108_gb300 import mppi
+    probs = _mixed("bf16")[:2]
+    states = _states(probs, np.random.default_rng(2))
+    b = mppi.Batch(probs)
+    try:
+        b.inject_stall(True)
+        with pytest.raises(mppi.MppiError) as e:
+            b.step(states)
+        assert e.value.code == mppi.ETIMEOUT
+        b.inject_stall(False)
+        for i, p in enumerate(probs):
+            b.set_controls(i, W.initial_controls(p))
+        b.step(states)  # the batch is usable again
+    finally:
+        b.close()
