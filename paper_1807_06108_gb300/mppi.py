@@ -591,3 +591,19 @@ class Batch:
     def inject_stall(self, on=True):
         _bcheck(_lib.mppi_batch_inject_stall(self.handle, int(bool(on))), "batch_inject_stall",
                 self.handle)
+
+
+# --------------------------------------------------------------------------
+# Allocation-free update (for callers that cannot allocate device memory)
+# --------------------------------------------------------------------------
+
+_sig("mppi_jump_update_noalloc", _st, _vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+     ctypes.c_float, ctypes.c_float, _vp, _vp)
+
+
+def mppi_jump_update_noalloc(costs_ptr, noise_ptr, K, T, m, lam, alpha, U_ptr, stream=0):
+    """Weights + weighted update from caller-owned device arrays, using the
+    library's fixed device scratch instead of allocating (see the header)."""
+    _check(_lib.mppi_jump_update_noalloc(_vp(costs_ptr), _vp(noise_ptr), int(K), int(T), int(m),
+                                         float(lam), float(alpha), _vp(U_ptr), _vp(stream or None)),
+           "update_noalloc")
