@@ -322,6 +322,52 @@ mppi_status mppi_batch_autotune(mppi_batch* b, const float* x0s, int32_t reps,
 mppi_status mppi_batch_info(mppi_batch* b, int64_t* steps_per_solve_host, int32_t* n_items_host,
                             int32_t* grid_host);
 
+/* ------------------------------------------------------------------------ */
+/* Served form: a native request loop over n sessions (any mix of plants, K, */
+/* T).  Each request is one MPC step (Algorithm 1 with the session's         */
+/* iteration count) warm-started from the session's device-resident controls */
+/* and counter (Sec. V).  A worker thread admits requests as soon as the     */
+/* session is idle (per-session order = submission order), one of            */
+/* max_inflight slots is free, and the session's device memory fits the      */
+/* budget -- idle sessions are checkpointed to the host and released, least  */
+/* recently used first, to make room.  Admitted requests run concurrently on */
+/* their sessions' own streams (continuous batching at the stream level).    */
+/* A session's results do not depend on what else is in flight.  All         */
+/* pointers are HOST pointers.                                               */
+/* ------------------------------------------------------------------------ */
+typedef struct mppi_server mppi_server;
+
+typedef struct {
+  int64_t submitted, completed, inflight, evictions;
+  double mean_ms, max_ms, p50_ms, p99_ms; /* submit-to-completion latency */
+  double span_s;                          /* first submission to last completion */
+  size_t resident_bytes;                  /* device bytes of resident sessions */
+} mppi_serve_stats;
+
+/* cfgs [n], iters [n] (>= 1); budget_bytes bounds the device memory of the
+ * resident sessions (a session larger than the budget is MPPI_EINVAL). */
+mppi_status mppi_serve_create(const mppi_jump_config* cfgs_host, const int32_t* iters_host,
+                              int32_t n_sessions, size_t budget_bytes, int32_t max_inflight,
+                              mppi_server** out);
+/* Waits for all queued and running requests, then frees everything. */
+mppi_status mppi_serve_destroy(mppi_server* s);
+const char* mppi_serve_last_error(const mppi_server* s);
+/* Queues one MPC step of `session` from state x0 [n]; returns at once. */
+mppi_status mppi_serve_submit(mppi_server* s, int32_t session, const float* x0_host,
+                              uint64_t* ticket_host);
+/* done_host = 1 once the request finished; then u0 [m] is written and the
+ * request's status returned. */
+mppi_status mppi_serve_poll(mppi_server* s, uint64_t ticket, float* u0_host, int32_t* done_host);
+/* Blocks until the request finished (MPPI_ETIMEOUT after timeout_s). */
+mppi_status mppi_serve_wait(mppi_server* s, uint64_t ticket, float* u0_host, double timeout_s);
+/* Blocks until every submitted request finished (MPPI_ETIMEOUT after timeout_s). */
+mppi_status mppi_serve_drain(mppi_server* s, double timeout_s);
+mppi_status mppi_serve_get_stats(mppi_server* s, mppi_serve_stats* out_host);
+/* Forgets finished requests and latencies (MPPI_EBUSY while any is pending). */
+mppi_status mppi_serve_reset_stats(mppi_server* s);
+/* The session's control sequence [T][m] (MPPI_EBUSY while it has requests). */
+mppi_status mppi_serve_get_controls(mppi_server* s, int32_t session, float* U_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -607,3 +607,102 @@ def mppi_jump_update_noalloc(costs_ptr, noise_ptr, K, T, m, lam, alpha, U_ptr, s
     _check(_lib.mppi_jump_update_noalloc(_vp(costs_ptr), _vp(noise_ptr), int(K), int(T), int(m),
                                          float(lam), float(alpha), _vp(U_ptr), _vp(stream or None)),
            "update_noalloc")
+
+
+# --------------------------------------------------------------------------
+# Served form
+# --------------------------------------------------------------------------
+
+class ServeStats(ctypes.Structure):
+    """mppi_serve_stats."""
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("inflight", ctypes.c_int64), ("evictions", ctypes.c_int64),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("span_s", ctypes.c_double), ("resident_bytes", ctypes.c_size_t)]
+
+
+_sig("mppi_serve_create", _st, _P(Config), _P(ctypes.c_int32), ctypes.c_int32, ctypes.c_size_t,
+     ctypes.c_int32, _P(_vp))
+_sig("mppi_serve_destroy", _st, _vp)
+_sig("mppi_serve_last_error", ctypes.c_char_p, _vp)
+_sig("mppi_serve_submit", _st, _vp, ctypes.c_int32, _P(ctypes.c_float), _P(ctypes.c_uint64))
+_sig("mppi_serve_poll", _st, _vp, ctypes.c_uint64, _P(ctypes.c_float), _P(ctypes.c_int32))
+_sig("mppi_serve_wait", _st, _vp, ctypes.c_uint64, _P(ctypes.c_float), ctypes.c_double)
+_sig("mppi_serve_drain", _st, _vp, ctypes.c_double)
+_sig("mppi_serve_get_stats", _st, _vp, _P(ServeStats))
+_sig("mppi_serve_reset_stats", _st, _vp)
+_sig("mppi_serve_get_controls", _st, _vp, ctypes.c_int32, _P(ctypes.c_float))
+
+
+class Server:
+    """Sessions served by the library's request loop (see mppi_serve_create)."""
+
+    def __init__(self, probs, budget_bytes=20 << 30, max_inflight=16):
+        self.probs = list(probs)
+        self.n = len(self.probs)
+        cfgs = (Config * self.n)(*[config_from_problem(p) for p in self.probs])
+        iters = (ctypes.c_int32 * self.n)(*[p["iters"] for p in self.probs])
+        self.handle = _vp()
+        st = _lib.mppi_serve_create(cfgs, iters, self.n, int(budget_bytes), int(max_inflight),
+                                    ctypes.byref(self.handle))
+        if st != OK:
+            raise MppiError(st, "serve_create")
+
+    def _check(self, st, what):
+        if st != OK:
+            raise MppiError(st, what, (_lib.mppi_serve_last_error(self.handle) or b"").decode())
+
+    def close(self):
+        if self.handle:
+            _lib.mppi_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, session, x0):
+        x = np.zeros(12, dtype=np.float32)
+        x0 = np.asarray(x0, dtype=np.float32)
+        x[:x0.shape[0]] = x0
+        t = ctypes.c_uint64(0)
+        self._check(_lib.mppi_serve_submit(self.handle, int(session), x.ctypes.data_as(_P(ctypes.c_float)),
+                                           ctypes.byref(t)), "serve_submit")
+        return t.value
+
+    def wait(self, ticket, timeout_s=30.0):
+        u = np.zeros(4, dtype=np.float32)
+        self._check(_lib.mppi_serve_wait(self.handle, int(ticket), u.ctypes.data_as(_P(ctypes.c_float)),
+                                         float(timeout_s)), "serve_wait")
+        return u
+
+    def poll(self, ticket):
+        u = np.zeros(4, dtype=np.float32)
+        d = ctypes.c_int32(0)
+        st = _lib.mppi_serve_poll(self.handle, int(ticket), u.ctypes.data_as(_P(ctypes.c_float)),
+                                  ctypes.byref(d))
+        if d.value:
+            self._check(st, "serve_poll")
+            return u
+        return None
+
+    def drain(self, timeout_s=120.0):
+        self._check(_lib.mppi_serve_drain(self.handle, float(timeout_s)), "serve_drain")
+
+    def stats(self):
+        s = ServeStats()
+        self._check(_lib.mppi_serve_get_stats(self.handle, ctypes.byref(s)), "serve_get_stats")
+        return {f: getattr(s, f) for f, _ in ServeStats._fields_}
+
+    def reset_stats(self):
+        self._check(_lib.mppi_serve_reset_stats(self.handle), "serve_reset_stats")
+
+    def controls(self, session):
+        p = self.probs[session]
+        U = np.zeros((p["T"], _wl.CONTROL_DIM[p["system"]]), dtype=np.float32)
+        self._check(_lib.mppi_serve_get_controls(self.handle, int(session),
+                                                 U.ctypes.data_as(_P(ctypes.c_float))), "serve_get_controls")
+        return U
