@@ -93,7 +93,8 @@ def problem(system, K, T, dt, *, sigma, nu, mark_scale, mark_law="normal",
     if u_init is None:
         u_init = [0.0] if system == "cartpole" else [prm["mass"] * prm["g"] / 4.0] * 4
     return {
-        "name": name or f"{system}_K{K}_T{T}",
+        "name": name or (f"{system}_K{K}_T{T}_it{iters}"
+                         + ("_bf16" if noise_dtype == "bf16" else "")),
         "system": system,
         "K": int(K),
         "T": int(T),
@@ -157,8 +158,7 @@ def cartpole_k1000(K=1000, T=50, dt=0.02, **kw):
     """Cart-pole swing-up: K=1000 rollouts, T=50 steps of 0.02 s, one
     iteration, control noise N(0, 1.0^2), state jumps on (xdot, thetadot) at
     1.0/s with N(0, 0.5^2) marks, temperature 1.0, seed 0."""
-    args = dict(sigma=1.0, nu=1.0, mark_scale=0.5, lam=1.0, seed=0, iters=1,
-                name="cartpole_K1000_T50")
+    args = dict(sigma=1.0, nu=1.0, mark_scale=0.5, lam=1.0, seed=0, iters=1)
     args.update(kw)
     return problem("cartpole", K, T, dt, **args)
 
@@ -167,8 +167,7 @@ def quadrotor_k4096(K=4096, T=100, dt=0.01, **kw):
     """Quadrotor waypoint flight: K=4096, T=100 steps of 0.01 s, 10 iterations
     per MPC step, rotor noise N(0, 0.2^2), velocity jumps at 2.0/s with
     N(0, 1.0^2) marks per axis, obstacle penalty 1e4, seed 0."""
-    args = dict(sigma=0.2, nu=2.0, mark_scale=1.0, lam=1.0, seed=0, iters=10,
-                name="quadrotor_K4096_T100_it10")
+    args = dict(sigma=0.2, nu=2.0, mark_scale=1.0, lam=1.0, seed=0, iters=10)
     args.update(kw)
     return problem("quadrotor", K, T, dt, **args)
 
@@ -177,7 +176,7 @@ def large_quadrotor(K=65536, T=200, dt=0.005, **kw):
     """Large quadrotor: K=65536, T=200 steps of 0.005 s, 5 iterations,
     Laplace(0, 1.0) velocity-jump marks at 5.0/s, bfloat16 noise storage."""
     args = dict(sigma=0.2, nu=5.0, mark_scale=1.0, mark_law="laplace", lam=1.0, seed=0,
-                iters=5, noise_dtype="bf16", name="quadrotor_K65536_T200_it5_bf16")
+                iters=5, noise_dtype="bf16")
     args.update(kw)
     return problem("quadrotor", K, T, dt, **args)
 
