@@ -33,6 +33,7 @@ IterBuffers ctx_buffers(mppi_jump_ctx* ctx, float* costs, int set) {
   b.w = ctx->w;
   b.partial = ctx->partial;
   b.zpart = ctx->zpart;
+  b.gpart = ctx->gpart;
   b.rho_key = ctx->rho_key;
   b.done = ctx->done;
   b.cconst = ctx->scal;
@@ -55,8 +56,8 @@ void drop_graphs(mppi_jump_ctx* ctx) {
 namespace {
 
 struct Layout {
-  size_t x0, U, noise[2], counts[2], jrec[2], s_part, w, partial, zpart, scal, status, it, rho_key,
-      done, u0, total;
+  size_t x0, U, noise[2], counts[2], jrec[2], s_part, w, partial, zpart, gpart, scal, status, it,
+      rho_key, done, u0, total;
 };
 
 Layout layout_of(const DevProblem& P, const UpdateGeom& g) {
@@ -79,12 +80,13 @@ Layout layout_of(const DevProblem& P, const UpdateGeom& g) {
   L.s_part = take(sizeof(float) * P.Kpad);
   L.w = take(sizeof(float) * P.Kpad);
   L.partial = take(sizeof(float) * (size_t)g.chunks * P.T * P.m);
-  L.zpart = take(sizeof(float) * (size_t)g.chunks);
+  L.zpart = take(sizeof(float) * (size_t)g.groups * g.chunks);
+  L.gpart = take(sizeof(float) * (size_t)g.groups * (P.m + 1));
   L.scal = take(sizeof(float) * 8);
   L.status = take(sizeof(int) * 4);
   L.it = take(sizeof(uint32_t) * 4);
   L.rho_key = take(sizeof(uint32_t) * 4);
-  L.done = take(sizeof(unsigned) * 4);
+  L.done = take(sizeof(unsigned) * (4 + (size_t)g.groups));
   L.u0 = take(sizeof(float) * 4);
   L.total = off;
   return L;
@@ -245,6 +247,7 @@ mppi_status mppi_jump_init(const mppi_jump_config* cfg, void* stream, mppi_jump_
       ctx->w = (float*)(a + L.w);
       ctx->partial = (float*)(a + L.partial);
       ctx->zpart = (float*)(a + L.zpart);
+      ctx->gpart = (float*)(a + L.gpart);
       ctx->scal = (float*)(a + L.scal);
       ctx->status = (int*)(a + L.status);
       ctx->it = (uint32_t*)(a + L.it);

@@ -126,8 +126,13 @@ __device__ __forceinline__ UpdateArgs update_args(const BatchInst& I, int r) {
     u.inv_sigma2[i] = P.inv_sigma2[i];
     u.u_init[i] = P.u_init[i];
   }
+  u.chunks = I.chunks;
+  u.groups = I.groups;
   u.partial = I.partial;
   u.zpart = I.zpart;
+  u.gdone = nullptr;  // the work list orders the combine after every W item
+  u.edge = nullptr;
+  u.cpart = nullptr;
   u.e_out = I.e;
   u.U = I.U;
   const bool last = r == I.iters - 1;
@@ -154,8 +159,14 @@ __device__ void run_rollout_item(const BatchInst& I, int r, int tile) {
 
 template <int NT, bool BF16>
 __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
-  __shared__ UpdateShared<NT, 4> sh4;
-  __shared__ UpdateShared<NT, 1> sh1;
+  // one shared scratch, viewed per channel count
+  __shared__ __align__(16) unsigned char sh_raw[
+      sizeof(UpdateShared<NT, chunk_rollouts<BF16, 4, kBatchVPT, NT>()>) >
+              sizeof(UpdateShared<NT, chunk_rollouts<BF16, 1, kBatchVPT, NT>()>)
+          ? sizeof(UpdateShared<NT, chunk_rollouts<BF16, 4, kBatchVPT, NT>()>)
+          : sizeof(UpdateShared<NT, chunk_rollouts<BF16, 1, kBatchVPT, NT>()>)];
+  auto& sh4 = *reinterpret_cast<UpdateShared<NT, chunk_rollouts<BF16, 4, kBatchVPT, NT>()>*>(sh_raw);
+  auto& sh1 = *reinterpret_cast<UpdateShared<NT, chunk_rollouts<BF16, 1, kBatchVPT, NT>()>*>(sh_raw);
   __shared__ int item_sh;
   __shared__ int go_sh;
   for (;;) {
@@ -199,10 +210,11 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
         if (ok) {
           const int j_begin = (int)w.b * I.rows;
           const int j_end = min(I.P.T, j_begin + I.rows);
+          float* zdst = w.b == 0 ? u.zpart + w.a : nullptr;
           if (I.P.m == 4)
-            update_partial_body<BF16, 4, kBatchVPT, NT>(u, rho, (int)w.a, j_begin, j_end, w.b == 0, sh4);
+            update_partial_body<BF16, 4, kBatchVPT, NT>(u, rho, (int)w.a, j_begin, j_end, w.b == 0, zdst, sh4);
           else
-            update_partial_body<BF16, 1, kBatchVPT, NT>(u, rho, (int)w.a, j_begin, j_end, w.b == 0, sh1);
+            update_partial_body<BF16, 1, kBatchVPT, NT>(u, rho, (int)w.a, j_begin, j_end, w.b == 0, zdst, sh1);
         }
         signal = I.done_W + r;
       } else {

@@ -28,12 +28,13 @@ struct mppi_jump_ctx {
   float* s_part = nullptr;      // [Kpad]
   float* w = nullptr;           // [Kpad] unnormalised weights
   float* partial = nullptr;     // [chunks][T][m]
-  float* zpart = nullptr;       // [chunks]
+  float* zpart = nullptr;       // [groups][chunks]
+  float* gpart = nullptr;       // [groups][m] edge values, [groups] control costs
   float* scal = nullptr;        // cconst, diag[3]
   int* status = nullptr;        // device status word
   uint32_t* it = nullptr;       // iteration counter
   uint32_t* rho_key = nullptr;  // running cost minimum
-  unsigned* done = nullptr;     // update completion ticket
+  unsigned* done = nullptr;     // update completion ticket, then [groups] group tickets
   float* u0 = nullptr;          // [m]
   // pinned host staging for the synchronous step
   float* h_x0 = nullptr;

@@ -60,9 +60,10 @@ struct IterBuffers {
   float* s_part;       // [Kpad] k-dependent cost part
   float* w;            // [Kpad] unnormalised weights e_k
   float* partial;      // [chunks][T][m]
-  float* zpart;        // [chunks]
+  float* zpart;        // [groups][chunks]
+  float* gpart;        // [groups][m] shifted edge values, then [groups] control costs
   uint32_t* rho_key;   // running minimum of the costs (order key)
-  unsigned* done;      // completion ticket of the update
+  unsigned* done;      // completion ticket of the update, then [groups] group tickets
   float* cconst;       // k-independent cost term
   float* diag;         // rho, Z, F
   int* status;

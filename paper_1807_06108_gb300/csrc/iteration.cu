@@ -149,16 +149,22 @@ UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms) {
   UpdateGeom g;
   const int E = bf16 ? 8 : 4;
   const int nvec = Kpad * m / E;
-  g.vpt = nvec >= 4 * kUpdateThreads ? 4 : (nvec >= 2 * kUpdateThreads ? 2 : 1);
-  g.chunks = (nvec + kUpdateThreads * g.vpt - 1) / (kUpdateThreads * g.vpt);
-  // enough blocks to cover every SM several times over: at small K each block
-  // is short, and latency (not bandwidth) sets the update's duration
+  constexpr int W = kUpdateThreads / 32;  // warps of a block, one row each at a time
+  const int row_sets = (T + W - 1) / W;
+  // the longest chunks that still give every SM several blocks: at small K
+  // each block is short, and latency (not bandwidth) sets the duration
   const int target = 4 * (num_sms > 0 ? num_sms : 152);
-  int groups = (target + g.chunks - 1) / g.chunks;
-  if (groups > T) groups = T;
-  if (groups < 1) groups = 1;
-  g.rows = (T + groups - 1) / groups;
-  g.groups = (T + g.rows - 1) / g.rows;
+  g.vpt = 1;
+  for (int v = 4; v >= 1; v /= 2) {
+    const int chunks = (nvec + kUpdateThreads * v - 1) / (kUpdateThreads * v);
+    if ((long long)chunks * row_sets >= target) {
+      g.vpt = v;
+      break;
+    }
+  }
+  g.chunks = (nvec + kUpdateThreads * g.vpt - 1) / (kUpdateThreads * g.vpt);
+  g.rows = W;
+  g.groups = row_sets;
   return g;
 }
 
@@ -287,8 +293,13 @@ cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const Updat
   a.lam = P.lam;
   a.alpha = P.alpha;
   for (int i = 0; i < 4; ++i) a.inv_sigma2[i] = P.inv_sigma2[i];
+  a.chunks = g.chunks;
+  a.groups = g.groups;
   a.partial = b.partial;
   a.zpart = b.zpart;
+  a.gdone = b.done + 4;
+  a.edge = b.gpart;
+  a.cpart = b.gpart + (size_t)g.groups * P.m;
   a.e_out = b.w;
   a.U = b.U;
   a.u0_out = u0;

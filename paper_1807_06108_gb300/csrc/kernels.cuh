@@ -403,13 +403,20 @@ __device__ __forceinline__ void warp_sum2(float& s, float& c) {
   }
 }
 
-// Shared scratch of the update bodies for NT threads and M channels.
-template <int NT, int M>
+// Shared scratch of the update bodies for NT threads: per-warp partial sums
+// and the weights of one chunk of rollouts (ECAP floats).
+template <int NT, int ECAP>
 struct UpdateShared {
-  float red_s[NT / 32][M], red_c[NT / 32][M];
   float sh_s[NT / 32], sh_c[NT / 32];
   unsigned ticket;
+  __align__(16) float e[ECAP];
 };
+
+// Rollouts per chunk of the weighted sum: NT * VPT 16-byte vectors of a row.
+template <bool BF16, int M, int VPT, int NT>
+__host__ __device__ constexpr int chunk_rollouts() {
+  return NT * VPT * ((BF16 ? 8 : 4) / M);
+}
 
 // Compensated sum over the block; every thread gets the result.
 template <int NT>
@@ -481,8 +488,12 @@ struct UpdateArgs {
   int K, Kpad, T, rows;
   float inv_lam, lam, alpha;
   float inv_sigma2[4];
+  int chunks, groups;
   float* partial;  // [chunks][T][M]
-  float* zpart;    // [chunks]
+  float* zpart;    // [groups][chunks] (one launch) or [chunks]
+  unsigned* gdone;  // [groups] completion tickets of the step groups
+  float* edge;     // [groups][M] shifted first-row values of each group
+  float* cpart;    // [groups] control cost of each group's rows
   float* e_out;    // [Kpad]
   float* U;        // [T][M]
   float* u0_out;   // [M] or NULL
@@ -496,104 +507,90 @@ struct UpdateArgs {
   float u_init[4];
 };
 
-template <bool BF16, int M, int VPT, int NT>
+template <bool BF16, int M, int VPT, int NT, class SH>
 __device__ __forceinline__ void update_partial_body(const UpdateArgs& a, float rho, int chunk,
-                                                    int j_begin, int j_end, bool write_z,
-                                                    UpdateShared<NT, M>& sh) {
+                                                    int j_begin, int j_end, bool write_e, float* zdst,
+                                                    SH& sh) {
   constexpr int E = BF16 ? 8 : 4;  // elements per 16-byte vector
   constexpr int RPV = E / M;       // rollouts per vector
   constexpr int W = NT / 32;
+  constexpr int CV = NT * VPT;     // vectors per chunk
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nvec = a.Kpad * M / E;
-  const int vbase = chunk * (NT * VPT) + tid;
-  const uint4* nv = reinterpret_cast<const uint4*>(a.noise);
-  // the first row's loads are issued before the weights are formed
-  uint4 buf[VPT];
-#pragma unroll
-  for (int t = 0; t < VPT; ++t) {
-    const int v = vbase + t * NT;
-    buf[t] = v < nvec && j_begin < j_end ? __ldcg(nv + (size_t)j_begin * nvec + v)
-                                         : make_uint4(0u, 0u, 0u, 0u);
-  }
-  float e[VPT][RPV];
+  const int v0 = chunk * CV;
+  const int nvc = min(CV, nvec - v0);  // vectors of this chunk
+  // the chunk's weights, once, into shared memory
   float zs = 0.0f, zc = 0.0f;
-#pragma unroll
-  for (int t = 0; t < VPT; ++t) {
-    const int v = vbase + t * NT;
-#pragma unroll
-    for (int r = 0; r < RPV; ++r) {
-      const int k = v * RPV + r;
-      e[t][r] = v < nvec ? expf((rho - __ldcg(a.s_part + k)) * a.inv_lam) : 0.0f;
-      if (write_z && v < nvec) {
-        a.e_out[k] = e[t][r];
-        two_sum_acc(zs, zc, e[t][r]);
-      }
-    }
+  for (int r = tid; r < nvc * RPV; r += NT) {
+    const int k = v0 * RPV + r;
+    const float e = expf((rho - __ldcg(a.s_part + k)) * a.inv_lam);
+    sh.e[r] = e;
+    if (write_e) a.e_out[k] = e;
+    two_sum_acc(zs, zc, e);
   }
-  if (write_z) {
-    const float z = block_sum2<NT>(zs, zc, sh.sh_s, sh.sh_c);
-    if (tid == 0) a.zpart[chunk] = z;
+  if (zdst) {
+    const float z = block_sum2<NT>(zs, zc, sh.sh_s, sh.sh_c);  // its barriers publish sh.e
+    if (tid == 0) *zdst = z;
+  } else {
+    __syncthreads();
   }
-  for (int j = j_begin; j < j_end; ++j) {
-    if (j > j_begin) {
-#pragma unroll
-      for (int t = 0; t < VPT; ++t) {
-        const int v = vbase + t * NT;
-        buf[t] = v < nvec ? __ldcg(nv + (size_t)j * nvec + v) : make_uint4(0u, 0u, 0u, 0u);
-      }
-    }
+  // every warp reduces whole rows of the chunk: no block barrier per row, and
+  // each lane keeps several independent 16-byte loads in flight
+  const uint4* nv = reinterpret_cast<const uint4*>(a.noise);
+  for (int j = j_begin + wid; j < j_end; j += W) {
+    const uint4* row = nv + (size_t)j * nvec + v0;
     float acc[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) acc[i] = 0.0f;
-#pragma unroll
-    for (int t = 0; t < VPT; ++t) {
+#pragma unroll 4
+    for (int v = lane; v < nvc; v += 32) {
+      const uint4 q = __ldcs(row + v);
       float val[E];
       if constexpr (BF16) {
-        const uint32_t wd[4] = {buf[t].x, buf[t].y, buf[t].z, buf[t].w};
+        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           val[2 * h] = __uint_as_float(wd[h] << 16);
           val[2 * h + 1] = __uint_as_float(wd[h] & 0xffff0000u);
         }
       } else {
-        val[0] = __uint_as_float(buf[t].x);
-        val[1] = __uint_as_float(buf[t].y);
-        val[2] = __uint_as_float(buf[t].z);
-        val[3] = __uint_as_float(buf[t].w);
+        val[0] = __uint_as_float(q.x);
+        val[1] = __uint_as_float(q.y);
+        val[2] = __uint_as_float(q.z);
+        val[3] = __uint_as_float(q.w);
+      }
+      float ew[RPV];
+      if constexpr (RPV == 1) {
+        ew[0] = sh.e[v];
+      } else if constexpr (RPV == 2) {
+        const float2 t = reinterpret_cast<const float2*>(sh.e)[v];
+        ew[0] = t.x;
+        ew[1] = t.y;
+      } else {
+#pragma unroll
+        for (int h = 0; h < RPV / 4; ++h) {
+          const float4 t = reinterpret_cast<const float4*>(sh.e)[v * (RPV / 4) + h];
+          ew[4 * h] = t.x;
+          ew[4 * h + 1] = t.y;
+          ew[4 * h + 2] = t.z;
+          ew[4 * h + 3] = t.w;
+        }
       }
 #pragma unroll
-      for (int q = 0; q < E; ++q) acc[q % M] = fmaf(e[t][q / M], val[q], acc[q % M]);
+      for (int q2 = 0; q2 < E; ++q2) acc[q2 % M] = fmaf(ew[q2 / M], val[q2], acc[q2 % M]);
     }
-    float cmp[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-      cmp[i] = 0.0f;
-      warp_sum2(acc[i], cmp[i]);
-    }
-    __syncthreads();
-    if (lane == 0) {
-#pragma unroll
-      for (int i = 0; i < M; ++i) {
-        sh.red_s[wid][i] = acc[i];
-        sh.red_c[wid][i] = cmp[i];
-      }
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-      for (int i = 0; i < M; ++i) {
-        float s = lane < W ? sh.red_s[lane][i] : 0.0f;
-        float c = lane < W ? sh.red_c[lane][i] : 0.0f;
-        warp_sum2(s, c);
-        if (lane == 0) a.partial[((size_t)chunk * a.T + j) * M + i] = s + c;
-      }
+      float c = 0.0f;
+      warp_sum2(acc[i], c);
+      if (lane == 0) a.partial[((size_t)chunk * a.T + j) * M + i] = acc[i] + c;
     }
   }
 }
 
-template <int M, int NT>
+template <int M, int NT, class SH>
 __device__ __forceinline__ void update_combine_body(const UpdateArgs& a, bool ok, float rho,
-                                                    int chunks, UpdateShared<NT, M>& sh) {
+                                                    int chunks, SH& sh) {
   const int tid = threadIdx.x;
   const int TM = a.T * M;
   float Z = 0.0f, C = 0.0f;
@@ -654,32 +651,144 @@ __device__ __forceinline__ void update_combine_body(const UpdateArgs& a, bool ok
   }
 }
 
-// One launch: block (c, g) runs the partial body for chunk c and steps
-// g*rows .., then takes a completion ticket (one atomic per block, no
-// waiting); the last block runs the combine body and re-arms the ticket.
+// Combine of step group g in the one-launch update, run by the last block of
+// the group to finish its partial sums: for the group's rows (one per warp
+// of a block, rows * M <= 32 outputs) N = sum_c partial[c], then
+// U_j <- U_j + alpha N_j / Z (Eq. 37 with the normalisation of Eq. 36), and
+// with the MPC shift the value of row j goes to row j - 1; the group's first
+// row goes to u0 (group 0) or to edge[g], written into the last row of group
+// g - 1 by the final block.  Also the control cost of the group's old rows.
+// Every block of a group computed the same z_c, so every group (and the final
+// block) obtains the same Z.
+template <int M, int NT, class SH>
+__device__ __forceinline__ void update_group_combine(const UpdateArgs& a, int g, SH& sh) {
+  constexpr int G = (NT / 32) * M;  // outputs of a group
+  constexpr int P = NT / G;         // partial sums per output
+  static_assert(G <= 32, "a group's outputs are handled by one warp");
+  const int tid = threadIdx.x;
+  const int TM = a.T * M;
+  const int o = tid % G, p = tid / G;
+  const int idx = g * a.rows * M + o;
+  float s = 0.0f, c = 0.0f;
+  if (idx < TM) {
+#pragma unroll 4
+    for (int ch = p; ch < a.chunks; ch += P) two_sum_acc(s, c, __ldcg(a.partial + (size_t)ch * TM + idx));
+  }
+  float zs = 0.0f, zc = 0.0f;
+  for (int ch = tid; ch < a.chunks; ch += NT) two_sum_acc(zs, zc, __ldcg(a.zpart + (size_t)g * a.chunks + ch));
+  sh.e[tid] = s + c;
+  const float Z = block_sum2<NT>(zs, zc, sh.sh_s, sh.sh_c);  // its barriers publish sh.e
+  if (tid < G) {  // warp 0
+    float ns = 0.0f, nc = 0.0f;
+#pragma unroll 4
+    for (int q = 0; q < P; ++q) two_sum_acc(ns, nc, sh.e[q * G + tid]);
+    float v = 0.0f, cs = 0.0f;
+    if (idx < TM) {
+      const float uo = __ldcg(a.U + idx);
+      v = uo + a.alpha * ((ns + nc) * (1.0f / Z));
+      cs = 0.5f * a.lam * (uo * a.inv_sigma2[tid % M] * uo);
+    }
+    __syncwarp(G == 32 ? 0xffffffffu : ((1u << G) - 1u));
+    // every read of the group's old rows is done before any write below
+    if (idx < TM) {
+      if (a.shift) {
+        if (tid >= M) a.U[idx - M] = v;
+        else if (g == 0) {
+          if (a.u0_out) a.u0_out[tid] = v;
+        } else {
+          a.edge[g * M + tid] = v;
+        }
+        if (idx >= TM - M) a.U[idx] = a.u_init[idx - (TM - M)];
+      } else {
+        a.U[idx] = v;
+      }
+    }
+    sh.e[tid] = cs;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float s2 = 0.0f, c2 = 0.0f;
+    for (int q = 0; q < G; ++q) two_sum_acc(s2, c2, sh.e[q]);
+    a.cpart[g] = s2 + c2;
+  }
+}
+
+// Final block of the one-launch update: the control cost C over all groups,
+// the shifted edge rows, the diagnostics (rho~ = rho + C, Z, free energy
+// F = rho~/lambda - ln(Z/K) of Eq. 36), the counter advance and re-arming of
+// the running minimum.
+template <int M, int NT, class SH>
+__device__ __forceinline__ void update_final_body(const UpdateArgs& a, bool ok, float rho, SH& sh) {
+  const int tid = threadIdx.x;
+  float C = 0.0f, Z = 0.0f;
+  if (ok) {
+    float cs = 0.0f, cc = 0.0f;
+    for (int g = tid; g < a.groups; g += NT) two_sum_acc(cs, cc, __ldcg(a.cpart + g));
+    C = block_sum2<NT>(cs, cc, sh.sh_s, sh.sh_c);
+    float zs = 0.0f, zc = 0.0f;
+    for (int ch = tid; ch < a.chunks; ch += NT) two_sum_acc(zs, zc, __ldcg(a.zpart + ch));
+    Z = block_sum2<NT>(zs, zc, sh.sh_s, sh.sh_c);
+    if (a.shift)
+      for (int q = tid; q < (a.groups - 1) * M; q += NT) {
+        const int g = 1 + q / M, i = q % M;
+        a.U[(size_t)(g * a.rows - 1) * M + i] = __ldcg(a.edge + g * M + i);
+      }
+  } else if (a.shift && a.u0_out && tid < M) {
+    a.u0_out[tid] = __ldcg(a.U + tid);
+  }
+  if (tid == 0) {
+    if (ok) {
+      const float rf = rho + C;
+      a.diag[0] = rf;
+      a.diag[1] = Z;
+      a.diag[2] = rf * a.inv_lam - logf(Z / (float)a.K);
+    } else {
+      *a.status = kStatusNonFinite;
+    }
+    *a.it = *a.it + a.it_advance;
+    *a.rho_key = kKeyEmpty;
+  }
+}
+
+// One launch: block (c, g) runs the partial body for chunk c and the rows of
+// step group g, then takes its group's completion ticket (one atomic per
+// block, no waiting); the last block of a group combines the group's rows and
+// takes the launch's ticket, and the last group runs the final body.  The
+// tickets are re-armed by their last holders.
 template <bool BF16, int M, int VPT>
 __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const UpdateArgs a) {
-  __shared__ UpdateShared<kUpdateThreads, M> sh;
+  __shared__ UpdateShared<kUpdateThreads, chunk_rollouts<BF16, M, VPT, kUpdateThreads>()> sh;
   const uint32_t key = __ldcg(a.rho_key);
   const bool ok = key < kKeyInf;  // at least one finite cost
   const float rho = ok ? key_to_float(key) : 0.0f;
+  const int g = blockIdx.y;
   if (ok) {
-    const int j_begin = blockIdx.y * a.rows;
+    const int j_begin = g * a.rows;
     const int j_end = min(a.T, j_begin + a.rows);
-    update_partial_body<BF16, M, VPT, kUpdateThreads>(a, rho, blockIdx.x, j_begin, j_end,
-                                                      blockIdx.y == 0, sh);
+    update_partial_body<BF16, M, VPT, kUpdateThreads>(
+        a, rho, blockIdx.x, j_begin, j_end, g == 0, a.zpart + (size_t)g * a.chunks + blockIdx.x, sh);
   }
   // the barrier orders the block's stores before thread 0's fence and
-  // ticket; the winner fences again before reading the other partials
+  // ticket; each winner fences again before reading what the others wrote
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
+    sh.ticket = atomicAdd(a.gdone + g, 1u);
+  }
+  __syncthreads();
+  if (sh.ticket != gridDim.x - 1) return;
+  __threadfence();
+  if (ok) update_group_combine<M, kUpdateThreads>(a, g, sh);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.gdone[g] = 0u;
     __threadfence();
     sh.ticket = atomicAdd(a.done, 1u);
   }
   __syncthreads();
-  if (sh.ticket != gridDim.x * gridDim.y - 1) return;
+  if (sh.ticket != gridDim.y - 1) return;
   __threadfence();
-  update_combine_body<M, kUpdateThreads>(a, ok, rho, gridDim.x, sh);
+  update_final_body<M, kUpdateThreads>(a, ok, rho, sh);
   if (threadIdx.x == 0) *a.done = 0u;
 }
 
