@@ -58,6 +58,10 @@ NOISE_OPS_PER_STEP = {"cartpole": 79.0, "quadrotor": 218.0}
 L2_BYTES = 129 * 1024 * 1024
 
 
+VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged"}
+ROLLOUT_KERNELS = {1: "rollout_kernel", 2: "rollout_split_kernel", 3: "rollout_staged_kernel"}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -332,6 +336,8 @@ def run_ours(args):
     if args.autotune:
         tile, _ = mppi.mppi_jump_autotune(ctx, solver.x0.data_ptr(), iters, reps=5)
     else:
+        if args.tile:
+            mppi.mppi_jump_set_tuning(ctx, *[int(v) for v in args.tile.split(",")])
         tile = mppi.mppi_jump_get_tuning(ctx)
     for _ in range(args.warmup):  # warm-up (captures the graph)
         one_step()
@@ -427,7 +433,7 @@ def run_ours(args):
         "config": {"workload": prob["name"], "K": K, "T": T, "iters": iters, "dt": prob["dt"],
                    "noise": prob["noise_dtype"], "jump_rate": prob["nu"],
                    "solves_per_s": value / steps_per_solve,
-                   "rollout_tile": {"variant": "fused" if tile[0] == 1 else "split",
+                   "rollout_tile": {"variant": VARIANT_NAMES[tile[0]],
                                     "block": tile[1], "chunk": tile[2]},
                    "l2": "flushed between timed steps (write of 2x L2 size)"},
         "e2e": {"value": e2e, "unit": "trajectory-steps/s",
@@ -435,9 +441,9 @@ def run_ours(args):
                 "solves_per_s": e2e / steps_per_solve},
         # per iteration: noise + rollout + update kernels (split tile) or
         # rollout + update (fused tile), timed region A only
-        "gpu_launches": (3 if tile[0] == 2 else 2) * iters * args.steps,
+        "gpu_launches": (2 if tile[0] == 1 else 3) * iters * args.steps,
         "roofline": {"bound": "alu",
-                     "kernel": "rollout_split_kernel" if tile[0] == 2 else "rollout_kernel",
+                     "kernel": ROLLOUT_KERNELS[tile[0]],
                      "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
                      "frac": achieved / alu_peak, "traffic": None, "avg_launch_ms": roll_avg,
                      "peak_basis": f"{n_sms} SMs x 128 lanes x {sm_mhz:.0f} MHz "
@@ -466,6 +472,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="time the rollout tile the library's autotuner picks")
+    ap.add_argument("--tile", default="",
+                    help="rollout tile 'variant,block,chunk' (1 fused, 2 split, 3 staged)")
     ap.add_argument("--only", choices=["batched", "served"],
                     help="run only the batched or served measurement (for profiling)")
     args = ap.parse_args()

@@ -183,11 +183,15 @@ mppi_status mppi_jump_step_async(mppi_jump_ctx* ctx, const float* x0, int32_t it
  * one thread per rollout, draws the noise and rolls out; 2 = split: a noise
  * pass over K x T/4 threads stores delta_eff and the jump counts, then one
  * thread per rollout runs the sequential dynamics (more parallelism when K
- * alone does not fill the GPU).  rollout_block: threads per block of the
- * rollout kernel (32, 64, 96 or 128).  rollout_chunk: steps per unrolled
- * chunk of the split rollout, i.e. how many steps ahead its loads run (2, 4
- * or 8; ignored by the fused variant).  Every tile computes identical
- * results.  Setting a tile drops the cached graphs. */
+ * alone does not fill the GPU); 3 = staged: the split form with the step
+ * data of each block's rollouts moved into shared memory by bulk copies.
+ * rollout_block: threads per block of the rollout kernel (32, 64, 96 or
+ * 128).  rollout_chunk: for the split form, steps per unrolled chunk, i.e.
+ * how many steps ahead its loads run (2, 4 or 8); for the staged form, steps
+ * per shared-memory stage (4, 8 or 16); ignored by the fused form.  The
+ * default depends on K: split (128, 4) while the rollout blocks fit on the
+ * SMs about once, staged (128, 8) from two waves of blocks on.  Every tile
+ * computes identical results.  Setting a tile drops the cached graphs. */
 typedef struct {
   int32_t rollout_variant;
   int32_t rollout_block;

@@ -143,7 +143,37 @@ mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg) 
   return MPPI_OK;
 }
 
-cudaError_t prepare_kernels() { return cudaSuccess; }
+// Dynamic shared memory of the staged rollout: two stages of S steps of the
+// block's delta_eff rows, jump records and (q = 4) counts, plus two mbarriers.
+static size_t staged_smem_bytes(const DevProblem& P, int block, int S) {
+  const size_t sb = P.noise_bf16 ? 2 : 4;
+  const bool sj = P.jump_channel == MPPI_JUMP_STATE;
+  const size_t per_step = (size_t)block * (P.m * sb + (sj ? 16 : 0) + (sj && P.q > 3 ? 1 : 0));
+  return 2 * (size_t)S * per_step + 16;
+}
+
+constexpr int kStagedSmemMax = 160 * 1024;
+
+template <int SYS, bool BF16>
+static cudaError_t allow_staged_smem() {
+  cudaError_t e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 4>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 8>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
+  return e;
+}
+
+cudaError_t prepare_kernels() {
+  cudaError_t e = allow_staged_smem<0, false>();
+  if (e == cudaSuccess) e = allow_staged_smem<0, true>();
+  if (e == cudaSuccess) e = allow_staged_smem<1, false>();
+  if (e == cudaSuccess) e = allow_staged_smem<1, true>();
+  return e;
+}
 
 UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms) {
   UpdateGeom g;
@@ -168,19 +198,29 @@ UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms) {
   return g;
 }
 
+// Measured on GB300: with few rollout blocks per SM (K up to a few
+// thousand) the register-ring split form is fastest; with several waves of
+// blocks the staged form (bulk copies into shared memory, fewer registers,
+// more resident blocks) is.
 RolloutTile default_tile(const DevProblem& P, int num_sms) {
-  (void)P;
-  (void)num_sms;
+  const int sms = num_sms > 0 ? num_sms : 152;
+  const int blocks = (P.Kpad + 127) / 128;
   RolloutTile t;
-  t.variant = 2;
   t.block = 128;
-  t.chunk = 4;
+  if (blocks >= 2 * sms) {
+    t.variant = 3;
+    t.chunk = 8;
+  } else {
+    t.variant = 2;
+    t.chunk = 4;
+  }
   return t;
 }
 
 bool valid_tile(const RolloutTile& t) {
-  return (t.variant == 1 || t.variant == 2) && t.block >= 32 && t.block <= kRolloutThreads &&
-         t.block % 32 == 0 && (t.chunk == 2 || t.chunk == 4 || t.chunk == 8);
+  if (t.block < 32 || t.block > kRolloutThreads || t.block % 32 != 0) return false;
+  if (t.variant == 3) return t.chunk == 4 || t.chunk == 8 || t.chunk == 16;
+  return (t.variant == 1 || t.variant == 2) && (t.chunk == 2 || t.chunk == 4 || t.chunk == 8);
 }
 
 template <int M, bool BF16, bool DBG>
@@ -222,9 +262,38 @@ static void launch_seq_t(const DevProblem& P, const IterBuffers& b, const Rollou
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
 }
 
+template <int SYS, bool BF16>
+static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
+                                   cudaStream_t s) {
+  const int blocks = (P.Kpad + tile.block - 1) / tile.block;
+  const size_t smem = staged_smem_bytes(P, tile.block, tile.chunk);
+  if (smem > (size_t)kStagedSmemMax) return cudaErrorInvalidValue;
+  if (tile.chunk == 4)
+    rollout_staged_kernel<SYS, BF16, 4><<<blocks, tile.block, smem, s>>>(
+        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
+  else if (tile.chunk == 16)
+    rollout_staged_kernel<SYS, BF16, 16><<<blocks, tile.block, smem, s>>>(
+        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
+  else
+    rollout_staged_kernel<SYS, BF16, 8><<<blocks, tile.block, smem, s>>>(
+        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
+  return cudaSuccess;
+}
+
 cudaError_t launch_rollout_seq(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
                                cudaStream_t s) {
-  if (!valid_tile(tile)) return cudaErrorInvalidValue;
+  if (!valid_tile(tile) || tile.variant == 1) return cudaErrorInvalidValue;
+  if (tile.variant == 3) {
+    cudaError_t e = cudaSuccess;
+    switch (P.system * 2 + (P.noise_bf16 ? 1 : 0)) {
+      case 0: e = launch_staged_t<0, false>(P, b, tile, s); break;
+      case 1: e = launch_staged_t<0, true>(P, b, tile, s); break;
+      case 2: e = launch_staged_t<1, false>(P, b, tile, s); break;
+      default: e = launch_staged_t<1, true>(P, b, tile, s); break;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   switch (P.system * 2 + (P.noise_bf16 ? 1 : 0)) {
     case 0: launch_seq_t<0, false>(P, b, tile, s); break;
     case 1: launch_seq_t<0, true>(P, b, tile, s); break;
@@ -249,7 +318,7 @@ cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const Roll
     cudaError_t e = cudaMemsetAsync(b.rho_key, 0xff, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
   }
-  if (tile.variant == 2) {
+  if (tile.variant >= 2) {
     cudaError_t e = launch_noise(P, b, it_off, s);
     if (e != cudaSuccess) return e;
     return launch_rollout_seq(P, b, tile, s);

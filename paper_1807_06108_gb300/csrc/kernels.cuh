@@ -392,6 +392,189 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
 }
 
 // ---------------------------------------------------------------------------
+// Bulk copies into shared memory with mbarrier completion (sm_90+ PTX).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this thread's earlier shared-memory accesses before later
+// async-proxy (bulk copy) accesses to the same memory.
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of *bar to complete; false after limit_ns of wall
+// time (or 2^24 polls), so a copy that never lands cannot hang the kernel.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = timer_ns();
+  for (uint32_t it = 1; it < (1u << 24); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 31) == 0 && timer_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
+constexpr uint64_t kCopyWaitNs = 1000000000ull;  // 1 s
+constexpr int kStatusTimeout = 4;               // MPPI_ETIMEOUT
+
+// ---------------------------------------------------------------------------
+// Split form, part 2, staged.  rollout_staged_kernel: the same per-rollout
+// sequential dynamics as rollout_split_kernel, but the step data of the
+// block's rollouts (delta_eff rows, jump records, counts) is moved into shared
+// memory by the bulk-copy engine, S steps per stage, two stages in flight:
+// thread 0 issues the copies of stage s + 2 as soon as every thread is done
+// with stage s, and each thread reads its own step data from shared memory,
+// so the dependency chain of the dynamics never waits on a global load.  For
+// block b the rows are contiguous: step j covers elements
+// [j*Kpad + b*nt, j*Kpad + b*nt + nk) of every step-major array (nk = the
+// block's rollouts, a multiple of 32, so every copy is 16-byte aligned and a
+// multiple of 16 bytes).  Dynamic shared memory: 2 * S * nt * (m*s_b + 16 + 1)
+// bytes + 16 (the counts region only when q = 4).
+// ---------------------------------------------------------------------------
+template <int SYS, bool BF16, int S>
+__global__ void __launch_bounds__(kRolloutThreads)
+rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
+                      const void* __restrict__ noise, const uint8_t* __restrict__ counts,
+                      const float4* __restrict__ jrec, float* __restrict__ s_part,
+                      uint32_t* __restrict__ rho_key, int* __restrict__ status) {
+  constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
+  constexpr uint32_t SB = BF16 ? 2u : 4u;
+  extern __shared__ __align__(128) unsigned char stage_smem[];
+  const int nt = blockDim.x, tid = threadIdx.x;
+  const int k0 = blockIdx.x * nt;
+  const int k = k0 + tid;
+  const int nk = min(nt, P.Kpad - k0);
+  const bool mine = tid < nk;  // a rollout slot of this block (whole warps)
+  const bool active = k < P.K;
+  const bool sj = P.jump_channel == 0;
+  const bool q4 = P.q > 3;
+  const int T = P.T;
+  const uint32_t d_stride = (uint32_t)nt * m * SB, j_stride = sj ? (uint32_t)nt * 16u : 0u,
+                 c_stride = (sj && q4) ? (uint32_t)nt : 0u;
+  const uint32_t stage_bytes = S * (d_stride + j_stride + c_stride);
+  const uint32_t d_bytes = (uint32_t)nk * m * SB, j_bytes = sj ? (uint32_t)nk * 16u : 0u,
+                 c_bytes = (sj && q4) ? (uint32_t)nk : 0u;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage_smem + 2 * stage_bytes);
+  const int n_stages = (T + S - 1) / S;
+
+  auto issue = [&](int st) {  // thread 0 only
+    const int j0 = st * S;
+    const int ns = min(S, T - j0);
+    unsigned char* base = stage_smem + (st & 1) * stage_bytes;
+    uint64_t* bar = bars + (st & 1);
+    mbar_expect_tx(bar, (uint32_t)ns * (d_bytes + j_bytes + c_bytes));
+    for (int jj = 0; jj < ns; ++jj) {
+      const size_t row = (size_t)(j0 + jj) * P.Kpad + k0;
+      bulk_load(base + jj * d_stride, static_cast<const unsigned char*>(noise) + row * m * SB, d_bytes, bar);
+      if (j_bytes) bulk_load(base + S * d_stride + jj * j_stride, jrec + row, j_bytes, bar);
+      if (c_bytes)
+        bulk_load(base + S * (d_stride + j_stride) + jj * c_stride, counts + row, c_bytes, bar);
+    }
+  };
+
+  if (tid == 0) {
+    mbar_init(bars, 1);
+    mbar_init(bars + 1, 1);
+    mbar_init_fence();
+    fence_async_smem();
+  }
+  __syncthreads();
+  int issued = 0;  // stages whose copies thread 0 has issued
+  if (tid == 0) {
+    if (n_stages > 0) issue(issued++);
+    if (n_stages > 1) issue(issued++);
+  }
+
+  float x[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
+  float s = 0.0f, sc = 0.0f;
+  int st = 0;
+  bool aborted = false;
+  for (; st < n_stages; ++st) {
+    const int buf = st & 1;
+    const bool ok = mbar_wait_bounded(bars + buf, (uint32_t)(st >> 1) & 1u, kCopyWaitNs);
+    if (ok && mine && active) {
+      const unsigned char* base = stage_smem + buf * stage_bytes;
+      const int j0 = st * S;
+      const int ns = min(S, T - j0);
+#pragma unroll 2
+      for (int jj = 0; jj < ns; ++jj) {
+        const int j = j0 + jj;
+        float de[m], u[m];
+        load_noise<m, BF16>(base + jj * d_stride, tid, de);
+#pragma unroll
+        for (int i = 0; i < m; ++i) u[i] = __ldg(U + j * m + i);
+        float4 jr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        int cnt = 0;
+        if (sj) {
+          jr = reinterpret_cast<const float4*>(base + S * d_stride + jj * j_stride)[tid];
+          if (q4) cnt = base[S * (d_stride + j_stride) + jj * c_stride + tid];
+        }
+        const float J[4] = {jr.x, jr.y, jr.z, jr.w};
+        const bool jumped = sj && (q4 ? cnt > 0 : jr.w > 0.5f);
+        cost_and_step<SYS>(P, x, u, de, jumped, J, s, sc);
+      }
+    }
+    // every thread is done with this buffer (and agrees on an expiry)
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    if (tid == 0 && st + 2 < n_stages) {
+      fence_async_smem();
+      issue(issued++);
+    }
+  }
+  if (aborted) {
+    if (tid == 0) {
+      atomicExch(status, kStatusTimeout);
+      // let the copies still in flight (stages st .. issued-1, at most one
+      // pending phase per buffer) land before the block's shared memory is
+      // released -- bounded again
+      for (int ls = st; ls < issued; ++ls)
+        mbar_wait_bounded(bars + (ls & 1), (uint32_t)(ls >> 1) & 1u, kCopyWaitNs);
+    }
+    return;
+  }
+  if (mine) finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
+}
+
+// ---------------------------------------------------------------------------
 // Block reductions (NT threads per block)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void warp_sum2(float& s, float& c) {

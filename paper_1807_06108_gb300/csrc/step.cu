@@ -18,7 +18,7 @@ using namespace mj;
 namespace {
 
 mppi_status capture_step(mppi_jump_ctx* ctx, int iters, cudaGraphExec_t* exec) {
-  const bool split = ctx->tile.variant == 2;
+  const bool split = ctx->tile.variant >= 2;
   const size_t need_links = 2 * (size_t)iters + 2;
   while (ctx->links.size() < need_links) {
     cudaEvent_t ev;
@@ -192,7 +192,7 @@ mppi_status mppi_jump_step_async(mppi_jump_ctx* ctx, const float* x0, int32_t it
   if (ctx->timing) ctx->timed_iters = iters;
   CK(cudaMemcpyAsync(ctx->x0, x0, sizeof(float) * ctx->P.n, cudaMemcpyDefault, ctx->stream), "x0 copy");
   CK(cudaGraphLaunch(ex, ctx->stream), "graph launch");
-  ctx->last_set = ctx->tile.variant == 2 ? (iters - 1) & 1 : 0;
+  ctx->last_set = ctx->tile.variant >= 2 ? (iters - 1) & 1 : 0;
   if (u0)
     CK(cudaMemcpyAsync(u0, ctx->u0, sizeof(float) * ctx->P.m, cudaMemcpyDefault, ctx->stream), "u0 copy");
   return MPPI_OK;
@@ -208,7 +208,7 @@ mppi_status mppi_jump_step(mppi_jump_ctx* ctx, const float* x0_host, int32_t ite
   CK(cudaMemcpyAsync(ctx->x0, ctx->h_x0, sizeof(float) * ctx->P.n, cudaMemcpyHostToDevice, ctx->stream),
      "x0 copy");
   CK(cudaGraphLaunch(ex, ctx->stream), "graph launch");
-  ctx->last_set = ctx->tile.variant == 2 ? (iters - 1) & 1 : 0;
+  ctx->last_set = ctx->tile.variant >= 2 ? (iters - 1) & 1 : 0;
   CK(cudaMemcpyAsync(ctx->h_u0, ctx->u0, sizeof(float) * ctx->P.m, cudaMemcpyDeviceToHost, ctx->stream),
      "u0 copy");
   CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
@@ -241,9 +241,10 @@ mppi_status mppi_jump_autotune(mppi_jump_ctx* ctx, const float* x0, int32_t iter
     cudaEventDestroy(e0);
     return fail(ctx->err, MPPI_ECUDA, "autotune events");
   }
-  const RolloutTile cands[12] = {{2, 128, 4}, {2, 64, 4}, {2, 32, 4}, {2, 128, 2}, {2, 64, 2},
-                                 {2, 32, 2},  {2, 128, 8}, {2, 64, 8}, {2, 32, 8}, {1, 128, 4},
-                                 {1, 64, 4},  {1, 32, 4}};
+  const RolloutTile cands[] = {{2, 128, 4}, {2, 64, 4},  {2, 32, 4},  {2, 128, 2}, {2, 64, 2},
+                               {2, 32, 2},  {2, 128, 8}, {2, 64, 8},  {2, 32, 8},  {3, 128, 4},
+                               {3, 128, 8}, {3, 64, 8},  {3, 32, 8},  {3, 128, 16}, {3, 64, 16},
+                               {1, 128, 4}, {1, 64, 4},  {1, 32, 4}};
   RolloutTile best = ctx->tile;
   float best_ms = 1e30f;
   for (const RolloutTile& t : cands) {

@@ -41,12 +41,14 @@ def _one_iteration(prob, x0, U, it, tile):
     W.quadrotor_k4096(K=1100, T=41, nu=9.0),
     W.quadrotor_k4096(K=700, T=13, nu=9.0, jump_channel="control", noise_dtype="bf16",
                       mark_law="laplace"),
-], ids=["cartpole", "quadrotor_state", "quadrotor_control_bf16"])
+    W.quadrotor_k4096(K=300, T=21, nu=12.0, jump_rows=[3, 4, 5, 9], noise_dtype="bf16"),
+], ids=["cartpole", "quadrotor_state", "quadrotor_control_bf16", "quadrotor_q4_state_bf16"])
 def test_rollout_tiles_are_bit_identical(cuda, prob):
     rng = np.random.default_rng(0)
     x0, U = W.random_state(prob, rng, 0.1), W.random_controls(prob, rng, 0.2)
     ref = _one_iteration(prob, x0, U, 3, (1, 128, 4))
-    for tile in [(2, 128, 4), (2, 64, 2), (2, 32, 8), (1, 32, 4), (2, 96, 4)]:
+    for tile in [(2, 128, 4), (2, 64, 2), (2, 32, 8), (1, 32, 4), (2, 96, 4), (3, 128, 8),
+                 (3, 64, 4), (3, 32, 16), (3, 96, 8)]:
         got = _one_iteration(prob, x0, U, 3, tile)
         for a, b in zip(ref, got):
             np.testing.assert_array_equal(a, b)
@@ -56,7 +58,8 @@ def test_invalid_tile_rejected(cuda):
     from paper_1807_06108_gb300 import mppi
     s = _solver(W.cartpole_k1000(K=64, T=4))
     try:
-        for bad in [(0, 128, 4), (3, 128, 4), (2, 48, 4), (2, 256, 4), (1, 16, 4), (2, 64, 3)]:
+        for bad in [(0, 128, 4), (4, 128, 4), (3, 128, 2), (2, 128, 16), (2, 48, 4), (2, 256, 4),
+                    (1, 16, 4), (2, 64, 3)]:
             with pytest.raises(mppi.MppiError):
                 mppi.mppi_jump_set_tuning(s.ctx, *bad)
         assert mppi.mppi_jump_get_tuning(s.ctx) == (2, 128, 4)

@@ -62,6 +62,9 @@ def _cases():
     c["quadrotor_K33_T5_many_jumps"] = (p, W.random_state(p, r, 0.1), W.random_controls(p, r, 0.2), 77)
     p = W.quadrotor_k4096(K=96, T=4096, dt=0.001, lam=100.0)
     c["quadrotor_K96_T4096_max_horizon"] = (p, W.initial_state(p), W.initial_controls(p), 0)
+    p = W.quadrotor_k4096(K=515, T=27, nu=12.0, jump_rows=[3, 4, 5, 9], mark_scale=0.5)
+    r = rng(7)
+    c["quadrotor_q4_state_rows"] = (p, W.random_state(p, r, 0.1), W.random_controls(p, r, 0.2), 6)
     p = W.cartpole_k1000(K=5000, T=50, nu=0.0)
     c["cartpole_no_jumps"] = (p, W.initial_state(p), W.initial_controls(p), 4)
     return c
