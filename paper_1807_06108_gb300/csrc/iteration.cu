@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <utility>
 
 #include "internal.h"
 #include "kernels.cuh"
@@ -144,12 +145,12 @@ mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg) 
 }
 
 // Dynamic shared memory of the staged rollout: two stages of S steps of the
-// block's delta_eff rows, jump records and (q = 4) counts, plus two mbarriers.
+// block's delta_eff rows, jump records and (q = 4) counts, plus four mbarriers.
 static size_t staged_smem_bytes(const DevProblem& P, int block, int S) {
   const size_t sb = P.noise_bf16 ? 2 : 4;
   const bool sj = P.jump_channel == MPPI_JUMP_STATE;
   const size_t per_step = (size_t)block * (P.m * sb + (sj ? 16 : 0) + (sj && P.q > 3 ? 1 : 0));
-  return 2 * (size_t)S * per_step + 16;
+  return 2 * (size_t)S * per_step + 32;
 }
 
 constexpr int kStagedSmemMax = 160 * 1024;
@@ -196,6 +197,35 @@ UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms) {
   g.rows = W;
   g.groups = row_sets;
   return g;
+}
+
+// The rollout and the update are the sequential critical path of an MPC step;
+// the noise pass of the next iteration only fills idle issue slots beside
+// them.  They launch at the device's highest priority, so that the block
+// scheduler places their blocks first when the two compete for SMs.
+static int high_priority() {
+  static int prio = [] {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+    return greatest;
+  }();
+  return prio;
+}
+
+template <class... Params, class... Args>
+static void launch_hi(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                      Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = high_priority();
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Measured on GB300: with few rollout blocks per SM (K up to a few
@@ -252,13 +282,13 @@ static void launch_seq_t(const DevProblem& P, const IterBuffers& b, const Rollou
                          cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
   if (tile.chunk == 2)
-    rollout_split_kernel<SYS, BF16, 2><<<blocks, tile.block, 0, s>>>(
+    launch_hi(rollout_split_kernel<SYS, BF16, 2>, dim3(blocks), dim3(tile.block), 0, s,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
   else if (tile.chunk == 8)
-    rollout_split_kernel<SYS, BF16, 8><<<blocks, tile.block, 0, s>>>(
+    launch_hi(rollout_split_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block), 0, s,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
   else
-    rollout_split_kernel<SYS, BF16, 4><<<blocks, tile.block, 0, s>>>(
+    launch_hi(rollout_split_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block), 0, s,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
 }
 
@@ -269,13 +299,13 @@ static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, co
   const size_t smem = staged_smem_bytes(P, tile.block, tile.chunk);
   if (smem > (size_t)kStagedSmemMax) return cudaErrorInvalidValue;
   if (tile.chunk == 4)
-    rollout_staged_kernel<SYS, BF16, 4><<<blocks, tile.block, smem, s>>>(
+    launch_hi(rollout_staged_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block), smem, s,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
   else if (tile.chunk == 16)
-    rollout_staged_kernel<SYS, BF16, 16><<<blocks, tile.block, smem, s>>>(
+    launch_hi(rollout_staged_kernel<SYS, BF16, 16>, dim3(blocks), dim3(tile.block), smem, s,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
   else
-    rollout_staged_kernel<SYS, BF16, 8><<<blocks, tile.block, smem, s>>>(
+    launch_hi(rollout_staged_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block), smem, s,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
   return cudaSuccess;
 }
@@ -307,8 +337,8 @@ template <int SYS, bool BF16, bool DBG>
 static void launch_fused_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
                            uint32_t it_off, cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
-  rollout_kernel<SYS, BF16, DBG><<<blocks, tile.block, 0, s>>>(
-      P, b.x0, b.U, b.it, it_off, b.s_part, b.noise, b.rho_key, b.dbg_counts, b.dbg_J);
+  launch_hi(rollout_kernel<SYS, BF16, DBG>, dim3(blocks), dim3(tile.block), 0, s, P, b.x0, b.U, b.it,
+            it_off, b.s_part, b.noise, b.rho_key, b.dbg_counts, b.dbg_J);
 }
 
 cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
@@ -339,7 +369,7 @@ cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const Roll
 
 template <bool BF16, int M, int VPT>
 static void launch_update_t(const UpdateArgs& a, const UpdateGeom& g, cudaStream_t s) {
-  update_kernel<BF16, M, VPT><<<dim3(g.chunks, g.groups), kUpdateThreads, 0, s>>>(a);
+  launch_hi(update_kernel<BF16, M, VPT>, dim3(g.chunks, g.groups), dim3(kUpdateThreads), 0, s, a);
 }
 
 template <bool BF16, int M>

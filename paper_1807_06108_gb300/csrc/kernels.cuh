@@ -40,23 +40,28 @@ __device__ __forceinline__ void publish_min_cost(float sk, uint32_t* rho_key) {
   if ((threadIdx.x & 31) == 0) atomicMin(rho_key, w);
 }
 
-// Summed marks of the jumps of one step (streams 2+n of the Philox counter).
+// Mark of the nj-th jump of step j (stream 2+nj of the Philox counter) added
+// to J.
+__device__ __forceinline__ void add_mark(const DevProblem& P, uint32_t k, uint32_t j, uint32_t it,
+                                         int nj, float J[4]) {
+  const uint4 wm = philox4x32_10(k, j, it, 2u + (uint32_t)nj, P.key0, P.key1);
+  if (P.mark_law == 0) {
+    float z[4];
+    normals4(wm, z);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < P.q) J[c] += P.mark_scale[c] * z[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < P.q) J[c] += laplace_mark(P.mark_scale[c], word_of(wm, c));
+  }
+}
+
+// Summed marks of the N jumps of one step, in jump order.
 __device__ __forceinline__ void draw_marks(const DevProblem& P, uint32_t k, uint32_t j, uint32_t it,
                                            int N, float J[4]) {
-  for (int nj = 0; nj < N; ++nj) {
-    const uint4 wm = philox4x32_10(k, j, it, 2u + (uint32_t)nj, P.key0, P.key1);
-    if (P.mark_law == 0) {
-      float z[4];
-      normals4(wm, z);
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (c < P.q) J[c] += P.mark_scale[c] * z[c];
-    } else {
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (c < P.q) J[c] += laplace_mark(P.mark_scale[c], word_of(wm, c));
-    }
-  }
+  for (int nj = 0; nj < N; ++nj) add_mark(P, k, j, it, nj, J);
 }
 
 template <int M, bool BF16>
@@ -285,13 +290,39 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
   const bool active = k < P.K;
   const uint32_t it = __ldg(it_ptr) + it_off;
   const uint32_t uk = (uint32_t)k;
+  const int ns = min(4, P.T - 4 * b);  // steps of this thread
   const uint4 wcount = philox4x32_10(uk, (uint32_t)b, it, 1u, P.key0, P.key1);
+  int N[4];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) N[jj] = jj < ns ? jump_count(P, word_of(wcount, jj)) : 0;
+  // Marks, one loop trip per jump in (step, jump) order: a warp runs the mark
+  // code as often as its busiest lane has jumps in its four steps, and the
+  // code exists once.  Each step's marks are summed in jump order, as in
+  // draw_marks.
+  float J[4][4];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) J[jj][c] = 0.0f;
+  const int c0 = N[0], c1 = c0 + N[1], c2 = c1 + N[2], total = c2 + N[3];
+#pragma unroll 1
+  for (int i = 0; i < total; ++i) {
+    const int jj = i < c0 ? 0 : (i < c1 ? 1 : (i < c2 ? 2 : 3));
+    const int first = jj == 0 ? 0 : (jj == 1 ? c0 : (jj == 2 ? c1 : c2));
+    float Jt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    add_mark(P, uk, (uint32_t)(4 * b + jj), it, i - first, Jt);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q == jj)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) J[q][c] += Jt[c];
+  }
   float zc[4];
   if constexpr (M == 1) normals4(philox4x32_10(uk, (uint32_t)b, it, 0u, P.key0, P.key1), zc);
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj) {
     const int j = 4 * b + jj;
-    if (j >= P.T) break;
+    if (jj >= ns) break;
     float de[M];
     if constexpr (M == 1) {
       de[0] = P.sqc_sigma[0] * zc[jj];
@@ -301,18 +332,15 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
 #pragma unroll
       for (int i = 0; i < M; ++i) de[i] = P.sqc_sigma[i] * z[i];
     }
-    const int N = jump_count(P, word_of(wcount, jj));
-    float J[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (N > 0) draw_marks(P, uk, (uint32_t)j, it, N, J);
     const size_t row = (size_t)j * P.Kpad + k;
     if (P.jump_channel == 1) {
-      if (N > 0) {
+      if (N[jj] > 0) {
 #pragma unroll
-        for (int i = 0; i < M; ++i) de[i] += J[i];
+        for (int i = 0; i < M; ++i) de[i] += J[jj][i];
       }
     } else {
-      const float4 rec = P.q > 3 ? make_float4(J[0], J[1], J[2], J[3])
-                                 : make_float4(J[0], J[1], J[2], (float)N);
+      const float4 rec = P.q > 3 ? make_float4(J[jj][0], J[jj][1], J[jj][2], J[jj][3])
+                                 : make_float4(J[jj][0], J[jj][1], J[jj][2], (float)N[jj]);
       jrec[row] = active ? rec : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     if constexpr (BF16) {
@@ -320,12 +348,14 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
       for (int i = 0; i < M; ++i) de[i] = __bfloat162float(__float2bfloat16_rn(de[i]));
     }
     store_noise<M, BF16>(noise, row, de, active);
-    counts[row] = active ? (uint8_t)N : (uint8_t)0;
+    counts[row] = active ? (uint8_t)N[jj] : (uint8_t)0;
     if (DBG && active) {
       const size_t rk = (size_t)j * P.K + k;
-      if (dbg_counts) dbg_counts[rk] = (uint8_t)N;
+      if (dbg_counts) dbg_counts[rk] = (uint8_t)N[jj];
       if (dbg_J)
-        for (int c = 0; c < P.q; ++c) dbg_J[rk * P.q + c] = J[c];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < P.q) dbg_J[rk * P.q + c] = J[jj][c];
     }
   }
 }
@@ -413,6 +443,9 @@ __device__ __forceinline__ void mbar_init_fence() {
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
@@ -455,15 +488,18 @@ constexpr int kStatusTimeout = 4;               // MPPI_ETIMEOUT
 // Split form, part 2, staged.  rollout_staged_kernel: the same per-rollout
 // sequential dynamics as rollout_split_kernel, but the step data of the
 // block's rollouts (delta_eff rows, jump records, counts) is moved into shared
-// memory by the bulk-copy engine, S steps per stage, two stages in flight:
-// thread 0 issues the copies of stage s + 2 as soon as every thread is done
-// with stage s, and each thread reads its own step data from shared memory,
-// so the dependency chain of the dynamics never waits on a global load.  For
+// memory by the bulk-copy engine, S steps per stage, two stages in flight.
+// Each stage buffer has a "full" mbarrier (the copies landed) and an "empty"
+// one (every warp of the block is done with it): a warp releases a buffer
+// and moves on to the next stage without waiting for the others; only thread
+// 0 waits for the release before it issues the copies of stage s + 2 into
+// the buffer.  Each thread reads its own step data from shared memory, so the
+// dependency chain of the dynamics never waits on a global load.  For
 // block b the rows are contiguous: step j covers elements
 // [j*Kpad + b*nt, j*Kpad + b*nt + nk) of every step-major array (nk = the
 // block's rollouts, a multiple of 32, so every copy is 16-byte aligned and a
 // multiple of 16 bytes).  Dynamic shared memory: 2 * S * nt * (m*s_b + 16 + 1)
-// bytes + 16 (the counts region only when q = 4).
+// bytes + 32 (the counts region only when q = 4).
 // ---------------------------------------------------------------------------
 template <int SYS, bool BF16, int S>
 __global__ void __launch_bounds__(kRolloutThreads)
@@ -488,14 +524,15 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
   const uint32_t stage_bytes = S * (d_stride + j_stride + c_stride);
   const uint32_t d_bytes = (uint32_t)nk * m * SB, j_bytes = sj ? (uint32_t)nk * 16u : 0u,
                  c_bytes = (sj && q4) ? (uint32_t)nk : 0u;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stage_smem + 2 * stage_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(stage_smem + 2 * stage_bytes);
+  uint64_t* empty = full + 2;
   const int n_stages = (T + S - 1) / S;
 
   auto issue = [&](int st) {  // thread 0 only
     const int j0 = st * S;
     const int ns = min(S, T - j0);
     unsigned char* base = stage_smem + (st & 1) * stage_bytes;
-    uint64_t* bar = bars + (st & 1);
+    uint64_t* bar = full + (st & 1);
     mbar_expect_tx(bar, (uint32_t)ns * (d_bytes + j_bytes + c_bytes));
     for (int jj = 0; jj < ns; ++jj) {
       const size_t row = (size_t)(j0 + jj) * P.Kpad + k0;
@@ -507,8 +544,10 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
   };
 
   if (tid == 0) {
-    mbar_init(bars, 1);
-    mbar_init(bars + 1, 1);
+    mbar_init(full, 1);
+    mbar_init(full + 1, 1);
+    mbar_init(empty, (uint32_t)(nt / 32));
+    mbar_init(empty + 1, (uint32_t)(nt / 32));
     mbar_init_fence();
     fence_async_smem();
   }
@@ -523,12 +562,19 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
 #pragma unroll
   for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
   float s = 0.0f, sc = 0.0f;
+  float u_next[m];
+#pragma unroll
+  for (int i = 0; i < m; ++i) u_next[i] = T > 0 ? __ldg(U + i) : 0.0f;
   int st = 0;
   bool aborted = false;
   for (; st < n_stages; ++st) {
     const int buf = st & 1;
-    const bool ok = mbar_wait_bounded(bars + buf, (uint32_t)(st >> 1) & 1u, kCopyWaitNs);
-    if (ok && mine && active) {
+    const uint32_t parity = (uint32_t)(st >> 1) & 1u;
+    if (!mbar_wait_bounded(full + buf, parity, kCopyWaitNs)) {
+      aborted = true;
+      break;
+    }
+    if (mine && active) {
       const unsigned char* base = stage_smem + buf * stage_bytes;
       const int j0 = st * S;
       const int ns = min(S, T - j0);
@@ -538,7 +584,10 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
         float de[m], u[m];
         load_noise<m, BF16>(base + jj * d_stride, tid, de);
 #pragma unroll
-        for (int i = 0; i < m; ++i) u[i] = __ldg(U + j * m + i);
+        for (int i = 0; i < m; ++i) {
+          u[i] = u_next[i];
+          if (j + 1 < T) u_next[i] = __ldg(U + (j + 1) * m + i);  // one step ahead
+        }
         float4 jr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         int cnt = 0;
         if (sj) {
@@ -550,25 +599,27 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
         cost_and_step<SYS>(P, x, u, de, jumped, J, s, sc);
       }
     }
-    // every thread is done with this buffer (and agrees on an expiry)
-    if (__syncthreads_or(!ok)) {
-      aborted = true;
-      break;
-    }
+    // this warp is done with the buffer
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(empty + buf);
     if (tid == 0 && st + 2 < n_stages) {
+      if (!mbar_wait_bounded(empty + buf, parity, kCopyWaitNs)) {
+        aborted = true;
+        break;
+      }
       fence_async_smem();
       issue(issued++);
     }
   }
   if (aborted) {
-    if (tid == 0) {
-      atomicExch(status, kStatusTimeout);
-      // let the copies still in flight (stages st .. issued-1, at most one
-      // pending phase per buffer) land before the block's shared memory is
-      // released -- bounded again
+    // a wait expired: report it; thread 0 lets the copies it still has in
+    // flight (stages st .. issued-1, at most one pending phase per buffer)
+    // land before it leaves -- bounded again.  The other threads' waits
+    // expire on their own.
+    atomicExch(status, kStatusTimeout);
+    if (tid == 0)
       for (int ls = st; ls < issued; ++ls)
-        mbar_wait_bounded(bars + (ls & 1), (uint32_t)(ls >> 1) & 1u, kCopyWaitNs);
-    }
+        mbar_wait_bounded(full + (ls & 1), (uint32_t)(ls >> 1) & 1u, kCopyWaitNs);
     return;
   }
   if (mine) finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
