@@ -140,6 +140,15 @@ def compare_iteration(prob, U_in, g, r, kc=None, check_update=True):
         report["free_energy_rel_err"] = float(abs(g["fe"][2] - r["diag"][2]) / max(1, abs(r["diag"][2])))
         assert report["update_rel_err"] <= U_RTOL, report
         assert abs(g["w"].sum() - 1.0) < 1e-5
+        # weights and free energy inherit the cost error: to first order
+        # |w_gpu / w_ref - 1| <= 2 max|dS| / lambda and |dF| <= 2 max|dS| / lambda
+        if report["cost_flips"] == 0:
+            dS = float(np.max(np.abs(Sg - Sr))) / prob["lam"]
+            big = r["w"] > 1e-6
+            wrel = float(np.max(np.abs(g["w"][big] / r["w"][big] - 1.0)))
+            report["weight_rel_err"] = wrel
+            assert wrel <= 2.0 * dS + 1e-5, (wrel, dS)
+            assert abs(g["fe"][2] - r["diag"][2]) <= 2.0 * dS + 1e-5 * max(1.0, abs(r["diag"][2]))
     return report
 
 
