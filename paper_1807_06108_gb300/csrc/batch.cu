@@ -333,11 +333,18 @@ void build_items(mppi_batch* b) {
     I.groups = (P.T + I.rows - 1) / I.rows;
     max_iters = std::max(max_iters, I.iters);
   }
-  // instances by decreasing sequential length, so the longest rollouts start first
+  // instances grouped by plant (the costlier quadrotor first), each group by
+  // decreasing horizon: the longest rollouts start first, and blocks that run
+  // at the same time mostly execute the same plant's code, which keeps the
+  // instruction cache warm
   std::vector<int> order(b->n);
   for (int i = 0; i < b->n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return b->hinst[x].P.T > b->hinst[y].P.T; });
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const DevProblem& px = b->hinst[x].P;
+    const DevProblem& py = b->hinst[y].P;
+    if (px.system != py.system) return px.system > py.system;
+    return px.T > py.T;
+  });
   for (int r = 0; r < max_iters; ++r) {
     for (int i : order)
       if (r < b->hinst[i].iters)
