@@ -753,6 +753,20 @@ __device__ __forceinline__ void update_partial_body(const UpdateArgs& a, float r
   const int nvec = a.Kpad * M / E;
   const int v0 = chunk * CV;
   const int nvc = min(CV, nvec - v0);  // vectors of this chunk
+  constexpr int B = 4;                 // 16-byte loads in flight per lane
+  const uint4* nv = reinterpret_cast<const uint4*>(a.noise);
+  // the first loads of the warp's first row go out before the weights are
+  // formed (they do not depend on them), so their latency overlaps that phase
+  const int j_first = j_begin + wid;
+  uint4 q[B];
+  if (j_first < j_end) {
+    const uint4* row = nv + (size_t)j_first * nvec + v0;
+#pragma unroll
+    for (int h = 0; h < B; ++h) {
+      const int v = lane + 32 * h;
+      q[h] = v < nvc ? __ldcs(row + v) : make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
   // the chunk's weights, once, into shared memory
   float zs = 0.0f, zc = 0.0f;
   for (int r = tid; r < nvc * RPV; r += NT) {
@@ -769,49 +783,58 @@ __device__ __forceinline__ void update_partial_body(const UpdateArgs& a, float r
     __syncthreads();
   }
   // every warp reduces whole rows of the chunk: no block barrier per row, and
-  // each lane keeps several independent 16-byte loads in flight
-  const uint4* nv = reinterpret_cast<const uint4*>(a.noise);
-  for (int j = j_begin + wid; j < j_end; j += W) {
+  // each lane keeps B independent 16-byte loads in flight
+  for (int j = j_first; j < j_end; j += W) {
     const uint4* row = nv + (size_t)j * nvec + v0;
     float acc[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) acc[i] = 0.0f;
-#pragma unroll 4
-    for (int v = lane; v < nvc; v += 32) {
-      const uint4 q = __ldcs(row + v);
-      float val[E];
-      if constexpr (BF16) {
-        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+    for (int base = 0; base < nvc; base += 32 * B) {
+      if (j != j_first || base != 0) {
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          val[2 * h] = __uint_as_float(wd[h] << 16);
-          val[2 * h + 1] = __uint_as_float(wd[h] & 0xffff0000u);
-        }
-      } else {
-        val[0] = __uint_as_float(q.x);
-        val[1] = __uint_as_float(q.y);
-        val[2] = __uint_as_float(q.z);
-        val[3] = __uint_as_float(q.w);
-      }
-      float ew[RPV];
-      if constexpr (RPV == 1) {
-        ew[0] = sh.e[v];
-      } else if constexpr (RPV == 2) {
-        const float2 t = reinterpret_cast<const float2*>(sh.e)[v];
-        ew[0] = t.x;
-        ew[1] = t.y;
-      } else {
-#pragma unroll
-        for (int h = 0; h < RPV / 4; ++h) {
-          const float4 t = reinterpret_cast<const float4*>(sh.e)[v * (RPV / 4) + h];
-          ew[4 * h] = t.x;
-          ew[4 * h + 1] = t.y;
-          ew[4 * h + 2] = t.z;
-          ew[4 * h + 3] = t.w;
+        for (int h = 0; h < B; ++h) {
+          const int v = base + lane + 32 * h;
+          q[h] = v < nvc ? __ldcs(row + v) : make_uint4(0u, 0u, 0u, 0u);
         }
       }
 #pragma unroll
-      for (int q2 = 0; q2 < E; ++q2) acc[q2 % M] = fmaf(ew[q2 / M], val[q2], acc[q2 % M]);
+      for (int h = 0; h < B; ++h) {
+        const int v = base + lane + 32 * h;
+        if (v >= nvc) continue;
+        float val[E];
+        if constexpr (BF16) {
+          const uint32_t wd[4] = {q[h].x, q[h].y, q[h].z, q[h].w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            val[2 * t] = __uint_as_float(wd[t] << 16);
+            val[2 * t + 1] = __uint_as_float(wd[t] & 0xffff0000u);
+          }
+        } else {
+          val[0] = __uint_as_float(q[h].x);
+          val[1] = __uint_as_float(q[h].y);
+          val[2] = __uint_as_float(q[h].z);
+          val[3] = __uint_as_float(q[h].w);
+        }
+        float ew[RPV];
+        if constexpr (RPV == 1) {
+          ew[0] = sh.e[v];
+        } else if constexpr (RPV == 2) {
+          const float2 t = reinterpret_cast<const float2*>(sh.e)[v];
+          ew[0] = t.x;
+          ew[1] = t.y;
+        } else {
+#pragma unroll
+          for (int t = 0; t < RPV / 4; ++t) {
+            const float4 w4 = reinterpret_cast<const float4*>(sh.e)[v * (RPV / 4) + t];
+            ew[4 * t] = w4.x;
+            ew[4 * t + 1] = w4.y;
+            ew[4 * t + 2] = w4.z;
+            ew[4 * t + 3] = w4.w;
+          }
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < E; ++q2) acc[q2 % M] = fmaf(ew[q2 / M], val[q2], acc[q2 % M]);
+      }
     }
 #pragma unroll
     for (int i = 0; i < M; ++i) {
@@ -990,7 +1013,7 @@ __device__ __forceinline__ void update_final_body(const UpdateArgs& a, bool ok, 
 // takes the launch's ticket, and the last group runs the final body.  The
 // tickets are re-armed by their last holders.
 template <bool BF16, int M, int VPT>
-__global__ void __launch_bounds__(kUpdateThreads) update_kernel(const UpdateArgs a) {
+__global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateArgs a) {
   __shared__ UpdateShared<kUpdateThreads, chunk_rollouts<BF16, M, VPT, kUpdateThreads>()> sh;
   const uint32_t key = __ldcg(a.rho_key);
   const bool ok = key < kKeyInf;  // at least one finite cost
