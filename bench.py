@@ -58,6 +58,16 @@ NOISE_OPS_PER_STEP = {"cartpole": 79.0, "quadrotor": 218.0}
 L2_BYTES = 129 * 1024 * 1024
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
+# it stands (profiles/quadrotor_K4096_T100_it10_kernels.md,
+# profiles/quadrotor_K65536_T200_it5_bf16_kernels.md); None where no capture
+# of the current kernel exists.
+NCU_TRAFFIC = {
+    ("quadrotor_K4096_T100_it10", "rollout_split_kernel"): 13137920 + 0,
+    ("quadrotor_K65536_T200_it5_bf16", "rollout_staged_kernel"): 314639104 + 3260928,
+    ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105194240 + 3818240,
+}
+
 VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged"}
 ROLLOUT_KERNELS = {1: "rollout_kernel", 2: "rollout_split_kernel", 3: "rollout_staged_kernel"}
 
@@ -416,6 +426,25 @@ def run_ours(args):
     e2e_s = D.max_over_ranks(dist, time.perf_counter() - t0, "cuda")
     clk.__exit__(None, None, None)
     e2e = ws * steps_per_solve * args.steps / e2e_s
+
+    # ---- region D: the update kernel on its own (same launch configuration):
+    # inside the step it shares the GPU with the next iteration's noise pass,
+    # which blurs its bandwidth figure.  Each launch follows a fresh
+    # rollout_cost (which arms the running minimum) and an L2 flush.
+    n_iso = min(args.steps, 50)
+    iso_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n_iso)]
+    for i in range(n_iso + 3):
+        solver.rollout_cost(x0, want_costs=False)
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+            if i >= 3:
+                iso_ev[i - 3][0].record(stream)
+            mppi.mppi_jump_update(ctx)
+            if i >= 3:
+                iso_ev[i - 3][1].record(stream)
+    stream.synchronize()
+    upd_iso_ms = sum(a.elapsed_time(b) for a, b in iso_ev) / n_iso
     solver.close()
 
     peaks, peak_kind = _peaks()
@@ -429,7 +458,7 @@ def run_ours(args):
     sb = 2 if prob["noise_dtype"] == "bf16" else 4
     m = 1 if prob["system"] == "cartpole" else 4
     upd_bytes = K * T * m * sb + 8 * K + 8 * T * m
-    upd_gbs = upd_bytes / (upd_avg / 1e3) / 1e9
+    upd_gbs = upd_bytes / (upd_iso_ms / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     clocks = clk.summary()
     if rank != 0:
@@ -470,14 +499,19 @@ def run_ours(args):
         "roofline": {"bound": "alu",
                      "kernel": ROLLOUT_KERNELS[tile[0]],
                      "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
-                     "frac": achieved / alu_peak, "traffic": None, "avg_launch_ms": roll_avg,
+                     "frac": achieved / alu_peak,
+                     "traffic": NCU_TRAFFIC.get((prob["name"], ROLLOUT_KERNELS[tile[0]])),
+                     "avg_launch_ms": roll_avg,
                      "peak_basis": f"{n_sms} SMs x 128 lanes x {sm_mhz:.0f} MHz "
                                    f"({peak_kind} max clock)",
                      "ops_per_trajectory_step": ops_step},
         "roofline_update": {"bound": "hbm", "kernel": "update_kernel", "achieved": upd_gbs,
                             "peak": hbm, "unit": "GB/s", "frac": upd_gbs / hbm,
-                            "avg_launch_ms": upd_avg, "algorithmic_bytes": upd_bytes,
-                            "note": f"{peak_kind} peak; the noise is L2-resident at this size"},
+                            "avg_launch_ms": upd_iso_ms, "algorithmic_bytes": upd_bytes,
+                            "in_step_avg_launch_ms": upd_avg,
+                            "traffic": NCU_TRAFFIC.get((prob["name"], "update_kernel")),
+                            "note": f"{peak_kind} peak; timed alone after an L2 flush "
+                                    "(in the step it overlaps the next noise pass)"},
         "clocks": clocks,
         "cpu_baseline": cpu,
         **extras,

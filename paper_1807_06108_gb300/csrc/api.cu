@@ -34,7 +34,8 @@ IterBuffers ctx_buffers(mppi_jump_ctx* ctx, float* costs, int set) {
   b.partial = ctx->partial;
   b.zpart = ctx->zpart;
   b.gpart = ctx->gpart;
-  b.rho_key = ctx->rho_key;
+  b.rho_key = ctx->rho_key + (set & 1);
+  b.rho_key_next = ctx->rho_key + ((set + 1) & 1);
   b.done = ctx->done;
   b.cconst = ctx->scal;
   b.diag = ctx->scal + 1;
@@ -260,7 +261,7 @@ mppi_status mppi_jump_init(const mppi_jump_config* cfg, void* stream, mppi_jump_
       ctx->h_u0 = ctx->h_x0 + 16;
       ctx->h_status = (int*)(ctx->h_x0 + 32);
       e = cudaMemsetAsync(ctx->arena, 0, L.total, ctx->stream);
-      if (e == cudaSuccess) e = cudaMemsetAsync(ctx->rho_key, 0xff, sizeof(uint32_t), ctx->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ctx->rho_key, 0xff, 2 * sizeof(uint32_t), ctx->stream);
     }
     if (e == cudaSuccess) {
       const size_t TM = (size_t)ctx->P.T * ctx->P.m;

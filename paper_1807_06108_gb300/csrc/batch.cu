@@ -141,6 +141,8 @@ __device__ __forceinline__ UpdateArgs update_args(const BatchInst& I, int r) {
   u.status = nullptr;  // set by the caller
   u.done = nullptr;
   u.rho_key = I.rho_key;
+  u.rho_key_next = nullptr;
+  u.need_final = 1;
   u.it = I.it;
   u.it_advance = last ? (uint32_t)I.iters : 0u;
   u.shift = last ? 1 : 0;

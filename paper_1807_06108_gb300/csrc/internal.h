@@ -63,6 +63,7 @@ struct IterBuffers {
   float* zpart;        // [groups][chunks]
   float* gpart;        // [groups][m] shifted edge values, then [groups] control costs
   uint32_t* rho_key;   // running minimum of the costs (order key)
+  uint32_t* rho_key_next;  // the running minimum of the next iteration
   unsigned* done;      // completion ticket of the update, then [groups] group tickets
   float* cconst;       // k-independent cost term
   float* diag;         // rho, Z, F

@@ -406,6 +406,8 @@ cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const Updat
   a.status = b.status;
   a.done = b.done;
   a.rho_key = b.rho_key;
+  a.rho_key_next = b.rho_key_next;
+  a.need_final = (shift || it_advance > 0) ? 1 : 0;
   a.it = b.it;
   a.it_advance = it_advance;
   a.shift = shift;

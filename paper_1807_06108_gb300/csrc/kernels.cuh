@@ -392,8 +392,16 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
     (void)slot_unused;
     const size_t row = (size_t)step * P.Kpad + k;
     load_noise<m, BF16>(noise, row, d);
+    if constexpr (m == 4) {  // U rows are 16-byte aligned
+      const float4 u4 = __ldg(reinterpret_cast<const float4*>(U) + step);
+      u[0] = u4.x;
+      u[1] = u4.y;
+      u[2] = u4.z;
+      u[3] = u4.w;
+    } else {
 #pragma unroll
-    for (int i = 0; i < m; ++i) u[i] = __ldg(U + step * m + i);
+      for (int i = 0; i < m; ++i) u[i] = __ldg(U + step * m + i);
+    }
     jr = sj ? __ldg(jrec + row) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     c = (sj && q4) ? (int)__ldg(counts + row) : 0;
   };
@@ -584,9 +592,17 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
         float de[m], u[m];
         load_noise<m, BF16>(base + jj * d_stride, tid, de);
 #pragma unroll
-        for (int i = 0; i < m; ++i) {
-          u[i] = u_next[i];
-          if (j + 1 < T) u_next[i] = __ldg(U + (j + 1) * m + i);  // one step ahead
+        for (int i = 0; i < m; ++i) u[i] = u_next[i];
+        if (j + 1 < T) {  // one step ahead
+          if constexpr (m == 4) {
+            const float4 u4 = __ldg(reinterpret_cast<const float4*>(U) + j + 1);
+            u_next[0] = u4.x;
+            u_next[1] = u4.y;
+            u_next[2] = u4.z;
+            u_next[3] = u4.w;
+          } else {
+            u_next[0] = __ldg(U + j + 1);
+          }
         }
         float4 jr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         int cnt = 0;
@@ -734,10 +750,12 @@ struct UpdateArgs {
   float* diag;     // rho, Z, F
   int* status;
   unsigned* done;
-  uint32_t* rho_key;
+  uint32_t* rho_key;       // running minimum of this iteration's costs
+  uint32_t* rho_key_next;  // the next iteration's, re-armed here (or NULL)
   uint32_t* it;
   uint32_t it_advance;
   int shift;
+  int need_final;  // run the final body even when every cost is finite
   float u_init[4];
 };
 
@@ -1011,10 +1029,16 @@ __device__ __forceinline__ void update_final_body(const UpdateArgs& a, bool ok, 
 // step group g, then takes its group's completion ticket (one atomic per
 // block, no waiting); the last block of a group combines the group's rows and
 // takes the launch's ticket, and the last group runs the final body.  The
-// tickets are re-armed by their last holders.
+// tickets are re-armed by their last holders.  An intermediate iteration of
+// an MPC step (no shift, no counter advance, every cost finite) needs no
+// final body: its diagnostics are overwritten by the next iteration.
 template <bool BF16, int M, int VPT>
 __global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateArgs a) {
   __shared__ UpdateShared<kUpdateThreads, chunk_rollouts<BF16, M, VPT, kUpdateThreads>()> sh;
+  // the next iteration's running minimum: its last reader (the previous
+  // update) has finished, and its next writer (the next rollout) has not begun
+  if (a.rho_key_next && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    *a.rho_key_next = kKeyEmpty;
   const uint32_t key = __ldcg(a.rho_key);
   const bool ok = key < kKeyInf;  // at least one finite cost
   const float rho = ok ? key_to_float(key) : 0.0f;
@@ -1036,6 +1060,10 @@ __global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateA
   if (sh.ticket != gridDim.x - 1) return;
   __threadfence();
   if (ok) update_group_combine<M, kUpdateThreads>(a, g, sh);
+  if (ok && !a.need_final) {  // an intermediate iteration: U is final here
+    if (threadIdx.x == 0) a.gdone[g] = 0u;
+    return;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     a.gdone[g] = 0u;
