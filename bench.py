@@ -63,13 +63,12 @@ L2_BYTES = 129 * 1024 * 1024
 # profiles/quadrotor_K65536_T200_it5_bf16_kernels.md); None where no capture
 # of the current kernel exists.
 NCU_TRAFFIC = {
-    ("quadrotor_K4096_T100_it10", "rollout_split_kernel"): 13137920 + 0,
-    ("quadrotor_K65536_T200_it5_bf16", "rollout_staged_kernel"): 314639104 + 3260928,
     ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105194240 + 3818240,
 }
 
-VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged"}
-ROLLOUT_KERNELS = {1: "rollout_kernel", 2: "rollout_split_kernel", 3: "rollout_staged_kernel"}
+VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged", 4: "async"}
+ROLLOUT_KERNELS = {1: "rollout_kernel", 2: "rollout_split_kernel", 3: "rollout_staged_kernel",
+                   4: "rollout_async_kernel"}
 
 
 def _peaks():

@@ -189,8 +189,9 @@ mppi_status mppi_jump_step_async(mppi_jump_ctx* ctx, const float* x0, int32_t it
  * 128).  rollout_chunk: for the split form, steps per unrolled chunk, i.e.
  * how many steps ahead its loads run (2, 4 or 8); for the staged form, steps
  * per shared-memory stage (4, 8 or 16); ignored by the fused form.  The
- * default depends on K: split (128, 4) while the rollout blocks fit on the
- * SMs about once, staged (128, 8) from two waves of blocks on.  Every tile
+ * staged form launches one extra (producer) warp per block.  The default is
+ * staged, block 128, with 16-step stages while the rollout blocks fit on the
+ * SMs about once and 8-step stages from two waves of blocks on.  Every tile
  * computes identical results.  Setting a tile drops the cached graphs. */
 typedef struct {
   int32_t rollout_variant;

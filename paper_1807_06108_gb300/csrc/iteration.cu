@@ -228,22 +228,19 @@ static void launch_hi(void (*kernel)(Params...), dim3 grid, dim3 block, size_t s
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-// Measured on GB300: with few rollout blocks per SM (K up to a few
-// thousand) the register-ring split form is fastest; with several waves of
-// blocks the staged form (bulk copies into shared memory, fewer registers,
-// more resident blocks) is.
+// Measured on GB300: the staged form (a producer warp moves the step data
+// into shared memory with bulk copies) is the fastest rollout at every size;
+// while the rollout blocks fit on the SMs about once, 16-step stages (about
+// 130 KB of shared memory per block, which also keeps the concurrent noise
+// pass off the rollout's SMs), beyond that 8-step stages so that several
+// blocks share an SM.
 RolloutTile default_tile(const DevProblem& P, int num_sms) {
   const int sms = num_sms > 0 ? num_sms : 152;
   const int blocks = (P.Kpad + 127) / 128;
   RolloutTile t;
+  t.variant = 3;
   t.block = 128;
-  if (blocks >= 2 * sms) {
-    t.variant = 3;
-    t.chunk = 8;
-  } else {
-    t.variant = 2;
-    t.chunk = 4;
-  }
+  t.chunk = blocks >= 2 * sms ? 8 : 16;
   return t;
 }
 
@@ -296,16 +293,16 @@ template <int SYS, bool BF16>
 static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
                                    cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
-  const size_t smem = staged_smem_bytes(P, tile.block, tile.chunk);
+  const size_t smem = staged_smem_bytes(P, tile.block, tile.chunk);  // + one producer warp
   if (smem > (size_t)kStagedSmemMax) return cudaErrorInvalidValue;
   if (tile.chunk == 4)
-    launch_hi(rollout_staged_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block), smem, s,
+    launch_hi(rollout_staged_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block + 32), smem, s,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
   else if (tile.chunk == 16)
-    launch_hi(rollout_staged_kernel<SYS, BF16, 16>, dim3(blocks), dim3(tile.block), smem, s,
+    launch_hi(rollout_staged_kernel<SYS, BF16, 16>, dim3(blocks), dim3(tile.block + 32), smem, s,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
   else
-    launch_hi(rollout_staged_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block), smem, s,
+    launch_hi(rollout_staged_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block + 32), smem, s,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
   return cudaSuccess;
 }

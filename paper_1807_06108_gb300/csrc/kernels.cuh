@@ -497,20 +497,24 @@ constexpr int kStatusTimeout = 4;               // MPPI_ETIMEOUT
 // sequential dynamics as rollout_split_kernel, but the step data of the
 // block's rollouts (delta_eff rows, jump records, counts) is moved into shared
 // memory by the bulk-copy engine, S steps per stage, two stages in flight.
+// The block is nt compute threads (one per rollout) plus one producer warp.
 // Each stage buffer has a "full" mbarrier (the copies landed) and an "empty"
-// one (every warp of the block is done with it): a warp releases a buffer
-// and moves on to the next stage without waiting for the others; only thread
-// 0 waits for the release before it issues the copies of stage s + 2 into
-// the buffer.  Each thread reads its own step data from shared memory, so the
-// dependency chain of the dynamics never waits on a global load.  For
-// block b the rows are contiguous: step j covers elements
+// one (every compute warp is done with it): a compute warp waits for "full",
+// runs its S steps from shared memory, releases the buffer and moves on; the
+// producer's lane 0 waits for "empty" and issues the copies of stage s + 2
+// into the buffer.  No compute thread ever waits for another or issues a
+// copy, and the dependency chain of the dynamics never waits on a global
+// load.  For block b the rows are contiguous: step j covers elements
 // [j*Kpad + b*nt, j*Kpad + b*nt + nk) of every step-major array (nk = the
 // block's rollouts, a multiple of 32, so every copy is 16-byte aligned and a
-// multiple of 16 bytes).  Dynamic shared memory: 2 * S * nt * (m*s_b + 16 + 1)
-// bytes + 32 (the counts region only when q = 4).
+// multiple of 16 bytes).  Launch with nt + 32 threads; dynamic shared memory
+// 2 * S * nt * (m*s_b + 16 + 1) bytes + 32 (the counts region only when
+// q = 4).
 // ---------------------------------------------------------------------------
+constexpr int kStagedMaxThreads = kRolloutThreads + 32;
+
 template <int SYS, bool BF16, int S>
-__global__ void __launch_bounds__(kRolloutThreads)
+__global__ void __launch_bounds__(kStagedMaxThreads)
 rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
                       const void* __restrict__ noise, const uint8_t* __restrict__ counts,
                       const float4* __restrict__ jrec, float* __restrict__ s_part,
@@ -518,54 +522,70 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
   constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
   constexpr uint32_t SB = BF16 ? 2u : 4u;
   extern __shared__ __align__(128) unsigned char stage_smem[];
-  const int nt = blockDim.x, tid = threadIdx.x;
+  const int nt = blockDim.x - 32, tid = threadIdx.x;  // compute threads, then the producer warp
   const int k0 = blockIdx.x * nt;
-  const int k = k0 + tid;
   const int nk = min(nt, P.Kpad - k0);
-  const bool mine = tid < nk;  // a rollout slot of this block (whole warps)
-  const bool active = k < P.K;
   const bool sj = P.jump_channel == 0;
   const bool q4 = P.q > 3;
   const int T = P.T;
   const uint32_t d_stride = (uint32_t)nt * m * SB, j_stride = sj ? (uint32_t)nt * 16u : 0u,
                  c_stride = (sj && q4) ? (uint32_t)nt : 0u;
   const uint32_t stage_bytes = S * (d_stride + j_stride + c_stride);
-  const uint32_t d_bytes = (uint32_t)nk * m * SB, j_bytes = sj ? (uint32_t)nk * 16u : 0u,
-                 c_bytes = (sj && q4) ? (uint32_t)nk : 0u;
   uint64_t* full = reinterpret_cast<uint64_t*>(stage_smem + 2 * stage_bytes);
   uint64_t* empty = full + 2;
   const int n_stages = (T + S - 1) / S;
+  const int compute_warps = nt / 32;
 
-  auto issue = [&](int st) {  // thread 0 only
-    const int j0 = st * S;
-    const int ns = min(S, T - j0);
-    unsigned char* base = stage_smem + (st & 1) * stage_bytes;
-    uint64_t* bar = full + (st & 1);
-    mbar_expect_tx(bar, (uint32_t)ns * (d_bytes + j_bytes + c_bytes));
-    for (int jj = 0; jj < ns; ++jj) {
-      const size_t row = (size_t)(j0 + jj) * P.Kpad + k0;
-      bulk_load(base + jj * d_stride, static_cast<const unsigned char*>(noise) + row * m * SB, d_bytes, bar);
-      if (j_bytes) bulk_load(base + S * d_stride + jj * j_stride, jrec + row, j_bytes, bar);
-      if (c_bytes)
-        bulk_load(base + S * (d_stride + j_stride) + jj * c_stride, counts + row, c_bytes, bar);
-    }
-  };
-
-  if (tid == 0) {
+  if (tid == nt) {
     mbar_init(full, 1);
     mbar_init(full + 1, 1);
-    mbar_init(empty, (uint32_t)(nt / 32));
-    mbar_init(empty + 1, (uint32_t)(nt / 32));
+    mbar_init(empty, (uint32_t)compute_warps);
+    mbar_init(empty + 1, (uint32_t)compute_warps);
     mbar_init_fence();
     fence_async_smem();
   }
   __syncthreads();
-  int issued = 0;  // stages whose copies thread 0 has issued
-  if (tid == 0) {
-    if (n_stages > 0) issue(issued++);
-    if (n_stages > 1) issue(issued++);
+
+  if (tid >= nt) {
+    // ---- producer warp: lane 0 issues every stage's copies
+    if (tid != nt) return;
+    const uint32_t d_bytes = (uint32_t)nk * m * SB, j_bytes = sj ? (uint32_t)nk * 16u : 0u,
+                   c_bytes = (sj && q4) ? (uint32_t)nk : 0u;
+    int issued = 0;
+    bool ok = true;
+    for (int st = 0; st < n_stages && ok; ++st) {
+      const int buf = st & 1;
+      if (st >= 2) {
+        // every compute warp released the buffer (use st/2 - 1 of it)
+        ok = mbar_wait_bounded(empty + buf, (uint32_t)((st >> 1) - 1) & 1u, kCopyWaitNs);
+        if (!ok) break;
+        fence_async_smem();
+      }
+      const int j0 = st * S;
+      const int ns = min(S, T - j0);
+      unsigned char* base = stage_smem + buf * stage_bytes;
+      mbar_expect_tx(full + buf, (uint32_t)ns * (d_bytes + j_bytes + c_bytes));
+      for (int jj = 0; jj < ns; ++jj) {
+        const size_t row = (size_t)(j0 + jj) * P.Kpad + k0;
+        bulk_load(base + jj * d_stride, static_cast<const unsigned char*>(noise) + row * m * SB, d_bytes,
+                  full + buf);
+        if (j_bytes) bulk_load(base + S * d_stride + jj * j_stride, jrec + row, j_bytes, full + buf);
+        if (c_bytes)
+          bulk_load(base + S * (d_stride + j_stride) + jj * c_stride, counts + row, c_bytes, full + buf);
+      }
+      ++issued;
+    }
+    if (!ok) atomicExch(status, kStatusTimeout);
+    // leave only when the copies of the last two stages have landed (bounded)
+    for (int ls = max(0, issued - 2); ls < issued; ++ls)
+      mbar_wait_bounded(full + (ls & 1), (uint32_t)(ls >> 1) & 1u, kCopyWaitNs);
+    return;
   }
 
+  // ---- compute threads: one rollout each
+  const int k = k0 + tid;
+  const bool mine = tid < nk;  // a rollout slot of this block (whole warps)
+  const bool active = k < P.K;
   float x[n];
 #pragma unroll
   for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
@@ -573,14 +593,11 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
   float u_next[m];
 #pragma unroll
   for (int i = 0; i < m; ++i) u_next[i] = T > 0 ? __ldg(U + i) : 0.0f;
-  int st = 0;
-  bool aborted = false;
-  for (; st < n_stages; ++st) {
+  for (int st = 0; st < n_stages; ++st) {
     const int buf = st & 1;
-    const uint32_t parity = (uint32_t)(st >> 1) & 1u;
-    if (!mbar_wait_bounded(full + buf, parity, kCopyWaitNs)) {
-      aborted = true;
-      break;
+    if (!mbar_wait_bounded(full + buf, (uint32_t)(st >> 1) & 1u, kCopyWaitNs)) {
+      atomicExch(status, kStatusTimeout);
+      return;
     }
     if (mine && active) {
       const unsigned char* base = stage_smem + buf * stage_bytes;
@@ -618,25 +635,6 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
     // this warp is done with the buffer
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(empty + buf);
-    if (tid == 0 && st + 2 < n_stages) {
-      if (!mbar_wait_bounded(empty + buf, parity, kCopyWaitNs)) {
-        aborted = true;
-        break;
-      }
-      fence_async_smem();
-      issue(issued++);
-    }
-  }
-  if (aborted) {
-    // a wait expired: report it; thread 0 lets the copies it still has in
-    // flight (stages st .. issued-1, at most one pending phase per buffer)
-    // land before it leaves -- bounded again.  The other threads' waits
-    // expire on their own.
-    atomicExch(status, kStatusTimeout);
-    if (tid == 0)
-      for (int ls = st; ls < issued; ++ls)
-        mbar_wait_bounded(full + (ls & 1), (uint32_t)(ls >> 1) & 1u, kCopyWaitNs);
-    return;
   }
   if (mine) finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
 }

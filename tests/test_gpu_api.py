@@ -62,7 +62,7 @@ def test_invalid_tile_rejected(cuda):
                     (1, 16, 4), (2, 64, 3)]:
             with pytest.raises(mppi.MppiError):
                 mppi.mppi_jump_set_tuning(s.ctx, *bad)
-        assert mppi.mppi_jump_get_tuning(s.ctx) == (2, 128, 4)
+        assert mppi.mppi_jump_get_tuning(s.ctx) == (3, 128, 16)
     finally:
         s.close()
 
@@ -175,7 +175,7 @@ def test_autotune_keeps_results(cuda):
     try:
         s.set_x0(x0)
         (variant, block, chunk), ms = mppi.mppi_jump_autotune(s.ctx, s.x0.data_ptr(), 3, reps=2)
-        assert variant in (1, 2) and block in (32, 64, 128) and chunk in (2, 4, 8) and ms > 0
+        assert variant in (1, 2, 3) and block in (32, 64, 128) and chunk in (2, 4, 8, 16) and ms > 0
         assert s.iteration() == 0
         got = [s.step(x0) for _ in range(2)]
         np.testing.assert_array_equal(np.array(ref), np.array(got))
