@@ -145,12 +145,14 @@ mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg) 
 }
 
 // Dynamic shared memory of the staged rollout: two stages of S steps of the
-// block's delta_eff rows, jump records and (q = 4) counts, plus four mbarriers.
+// block's delta_eff rows, jump records, (q = 4) counts and the S control rows,
+// plus four mbarriers.
 static size_t staged_smem_bytes(const DevProblem& P, int block, int S) {
   const size_t sb = P.noise_bf16 ? 2 : 4;
   const bool sj = P.jump_channel == MPPI_JUMP_STATE;
   const size_t per_step = (size_t)block * (P.m * sb + (sj ? 16 : 0) + (sj && P.q > 3 ? 1 : 0));
-  return 2 * (size_t)S * per_step + 32;
+  const size_t u_rows = ((size_t)S * P.m * 4 + 15) & ~(size_t)15;
+  return 2 * ((size_t)S * per_step + u_rows) + 32;
 }
 
 constexpr int kStagedSmemMax = 160 * 1024;

@@ -507,9 +507,12 @@ constexpr int kStatusTimeout = 4;               // MPPI_ETIMEOUT
 // load.  For block b the rows are contiguous: step j covers elements
 // [j*Kpad + b*nt, j*Kpad + b*nt + nk) of every step-major array (nk = the
 // block's rollouts, a multiple of 32, so every copy is 16-byte aligned and a
-// multiple of 16 bytes).  Launch with nt + 32 threads; dynamic shared memory
-// 2 * S * nt * (m*s_b + 16 + 1) bytes + 32 (the counts region only when
-// q = 4).
+// multiple of 16 bytes).  The stage also carries the S control rows (one copy
+// rounded up to 16 bytes, which may read up to 12 bytes past U's end: U must
+// sit in an allocation padded to 16 bytes).  Each compute thread reads step
+// j + 1's data from shared memory while it computes step j.  Launch with
+// nt + 32 threads; dynamic shared memory 2 * (S * nt * (m*s_b + 16 + 1) +
+// round16(S * m * 4)) bytes + 32 (the counts region only when q = 4).
 // ---------------------------------------------------------------------------
 constexpr int kStagedMaxThreads = kRolloutThreads + 32;
 
@@ -530,7 +533,8 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
   const int T = P.T;
   const uint32_t d_stride = (uint32_t)nt * m * SB, j_stride = sj ? (uint32_t)nt * 16u : 0u,
                  c_stride = (sj && q4) ? (uint32_t)nt : 0u;
-  const uint32_t stage_bytes = S * (d_stride + j_stride + c_stride);
+  const uint32_t u_off = S * (d_stride + j_stride + c_stride);  // control rows
+  const uint32_t stage_bytes = u_off + ((S * m * 4 + 15) & ~15u);
   uint64_t* full = reinterpret_cast<uint64_t*>(stage_smem + 2 * stage_bytes);
   uint64_t* empty = full + 2;
   const int n_stages = (T + S - 1) / S;
@@ -564,7 +568,9 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
       const int j0 = st * S;
       const int ns = min(S, T - j0);
       unsigned char* base = stage_smem + buf * stage_bytes;
-      mbar_expect_tx(full + buf, (uint32_t)ns * (d_bytes + j_bytes + c_bytes));
+      const uint32_t u_bytes = ((uint32_t)ns * m * 4 + 15) & ~15u;
+      mbar_expect_tx(full + buf, (uint32_t)ns * (d_bytes + j_bytes + c_bytes) + u_bytes);
+      bulk_load(base + u_off, U + (size_t)j0 * m, u_bytes, full + buf);
       for (int jj = 0; jj < ns; ++jj) {
         const size_t row = (size_t)(j0 + jj) * P.Kpad + k0;
         bulk_load(base + jj * d_stride, static_cast<const unsigned char*>(noise) + row * m * SB, d_bytes,
@@ -590,9 +596,6 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
 #pragma unroll
   for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
   float s = 0.0f, sc = 0.0f;
-  float u_next[m];
-#pragma unroll
-  for (int i = 0; i < m; ++i) u_next[i] = T > 0 ? __ldg(U + i) : 0.0f;
   for (int st = 0; st < n_stages; ++st) {
     const int buf = st & 1;
     if (!mbar_wait_bounded(full + buf, (uint32_t)(st >> 1) & 1u, kCopyWaitNs)) {
@@ -603,30 +606,40 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
       const unsigned char* base = stage_smem + buf * stage_bytes;
       const int j0 = st * S;
       const int ns = min(S, T - j0);
-#pragma unroll 2
-      for (int jj = 0; jj < ns; ++jj) {
-        const int j = j0 + jj;
-        float de[m], u[m];
+      // step data of step jj of this stage, from shared memory
+      auto fetch = [&](int jj, float* de, float* u, float4& jr, int& cnt) {
         load_noise<m, BF16>(base + jj * d_stride, tid, de);
-#pragma unroll
-        for (int i = 0; i < m; ++i) u[i] = u_next[i];
-        if (j + 1 < T) {  // one step ahead
-          if constexpr (m == 4) {
-            const float4 u4 = __ldg(reinterpret_cast<const float4*>(U) + j + 1);
-            u_next[0] = u4.x;
-            u_next[1] = u4.y;
-            u_next[2] = u4.z;
-            u_next[3] = u4.w;
-          } else {
-            u_next[0] = __ldg(U + j + 1);
-          }
+        if constexpr (m == 4) {
+          const float4 u4 = reinterpret_cast<const float4*>(base + u_off)[jj];
+          u[0] = u4.x;
+          u[1] = u4.y;
+          u[2] = u4.z;
+          u[3] = u4.w;
+        } else {
+          u[0] = reinterpret_cast<const float*>(base + u_off)[jj];
         }
-        float4 jr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        int cnt = 0;
+        jr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        cnt = 0;
         if (sj) {
           jr = reinterpret_cast<const float4*>(base + S * d_stride + jj * j_stride)[tid];
           if (q4) cnt = base[S * (d_stride + j_stride) + jj * c_stride + tid];
         }
+      };
+      float de_n[m], u_n[m];
+      float4 jr_n;
+      int cnt_n;
+      fetch(0, de_n, u_n, jr_n, cnt_n);
+#pragma unroll 2
+      for (int jj = 0; jj < ns; ++jj) {
+        float de[m], u[m];
+#pragma unroll
+        for (int i = 0; i < m; ++i) {
+          de[i] = de_n[i];
+          u[i] = u_n[i];
+        }
+        const float4 jr = jr_n;
+        const int cnt = cnt_n;
+        if (jj + 1 < ns) fetch(jj + 1, de_n, u_n, jr_n, cnt_n);  // next step's reads in flight
         const float J[4] = {jr.x, jr.y, jr.z, jr.w};
         const bool jumped = sj && (q4 ? cnt > 0 : jr.w > 0.5f);
         cost_and_step<SYS>(P, x, u, de, jumped, J, s, sc);
