@@ -63,8 +63,6 @@ L2_BYTES = 129 * 1024 * 1024
 # profiles/quadrotor_K65536_T200_it5_bf16_kernels.md); None where no capture
 # of the current kernel exists.
 NCU_TRAFFIC = {
-    ("quadrotor_K4096_T100_it10", "rollout_staged_kernel"): 13138688 + 0,
-    ("quadrotor_K65536_T200_it5_bf16", "rollout_staged_kernel"): 314692096 + 3012864,
     ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105189888 + 3017984,
 }
 
