@@ -76,9 +76,12 @@ struct IterBuffers {
 
 // Split variant, part 1: noise of iteration *it + it_off into b.noise etc.
 cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s);
-// Split variant, part 2: the sequential rollout over the stored noise.
+// Split variant, part 2: the sequential rollout over the stored noise.  pdl:
+// launch as a programmatic dependent of the previous kernel in the stream,
+// which must then not be the noise pass that wrote b.noise (the staged
+// rollout starts copying step data before it waits for that kernel).
 cudaError_t launch_rollout_seq(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
-                               cudaStream_t s);
+                               bool pdl, cudaStream_t s);
 // Whole rollout (either variant) of iteration *it + it_off.  arm_min resets
 // the running cost minimum first (the update re-arms it after every
 // iteration, so only a rollout that follows no update needs it).

@@ -204,7 +204,10 @@ UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms) {
 // The rollout and the update are the sequential critical path of an MPC step;
 // the noise pass of the next iteration only fills idle issue slots beside
 // them.  They launch at the device's highest priority, so that the block
-// scheduler places their blocks first when the two compete for SMs.
+// scheduler places their blocks first when the two compete for SMs, and as
+// programmatic dependents of the kernel before them in the stream, which
+// hides their launch latency (each kernel calls griddep_wait() before it
+// reads or writes anything the previous kernels touch).
 static int high_priority() {
   static int prio = [] {
     int least = 0, greatest = 0;
@@ -216,17 +219,22 @@ static int high_priority() {
 
 template <class... Params, class... Args>
 static void launch_hi(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                      Args&&... args) {
+                      bool pdl, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributePriority;
   attr[0].val.priority = high_priority();
+  // a programmatic dependent of the previous kernel in the stream: it may be
+  // scheduled once that kernel's blocks have all started, and waits in
+  // griddep_wait() for its completion before touching what it wrote
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 2 : 1;
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
@@ -278,56 +286,56 @@ cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_
 
 template <int SYS, bool BF16>
 static void launch_seq_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
-                         cudaStream_t s) {
+                         bool pdl, cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
   if (tile.chunk == 2)
-    launch_hi(rollout_split_kernel<SYS, BF16, 2>, dim3(blocks), dim3(tile.block), 0, s,
+    launch_hi(rollout_split_kernel<SYS, BF16, 2>, dim3(blocks), dim3(tile.block), 0, s, pdl,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
   else if (tile.chunk == 8)
-    launch_hi(rollout_split_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block), 0, s,
+    launch_hi(rollout_split_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block), 0, s, pdl,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
   else
-    launch_hi(rollout_split_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block), 0, s,
+    launch_hi(rollout_split_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block), 0, s, pdl,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
 }
 
 template <int SYS, bool BF16>
 static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
-                                   cudaStream_t s) {
+                                   bool pdl, cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
   const size_t smem = staged_smem_bytes(P, tile.block, tile.chunk);  // + one producer warp
   if (smem > (size_t)kStagedSmemMax) return cudaErrorInvalidValue;
   if (tile.chunk == 4)
-    launch_hi(rollout_staged_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block + 32), smem, s,
+    launch_hi(rollout_staged_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
   else if (tile.chunk == 16)
-    launch_hi(rollout_staged_kernel<SYS, BF16, 16>, dim3(blocks), dim3(tile.block + 32), smem, s,
+    launch_hi(rollout_staged_kernel<SYS, BF16, 16>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
   else
-    launch_hi(rollout_staged_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block + 32), smem, s,
+    launch_hi(rollout_staged_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
   return cudaSuccess;
 }
 
 cudaError_t launch_rollout_seq(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
-                               cudaStream_t s) {
+                               bool pdl, cudaStream_t s) {
   if (!valid_tile(tile) || tile.variant == 1) return cudaErrorInvalidValue;
   if (tile.variant == 3) {
     cudaError_t e = cudaSuccess;
     switch (P.system * 2 + (P.noise_bf16 ? 1 : 0)) {
-      case 0: e = launch_staged_t<0, false>(P, b, tile, s); break;
-      case 1: e = launch_staged_t<0, true>(P, b, tile, s); break;
-      case 2: e = launch_staged_t<1, false>(P, b, tile, s); break;
-      default: e = launch_staged_t<1, true>(P, b, tile, s); break;
+      case 0: e = launch_staged_t<0, false>(P, b, tile, pdl, s); break;
+      case 1: e = launch_staged_t<0, true>(P, b, tile, pdl, s); break;
+      case 2: e = launch_staged_t<1, false>(P, b, tile, pdl, s); break;
+      default: e = launch_staged_t<1, true>(P, b, tile, pdl, s); break;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
   switch (P.system * 2 + (P.noise_bf16 ? 1 : 0)) {
-    case 0: launch_seq_t<0, false>(P, b, tile, s); break;
-    case 1: launch_seq_t<0, true>(P, b, tile, s); break;
-    case 2: launch_seq_t<1, false>(P, b, tile, s); break;
-    default: launch_seq_t<1, true>(P, b, tile, s); break;
+    case 0: launch_seq_t<0, false>(P, b, tile, pdl, s); break;
+    case 1: launch_seq_t<0, true>(P, b, tile, pdl, s); break;
+    case 2: launch_seq_t<1, false>(P, b, tile, pdl, s); break;
+    default: launch_seq_t<1, true>(P, b, tile, pdl, s); break;
   }
   return cudaGetLastError();
 }
@@ -336,7 +344,7 @@ template <int SYS, bool BF16, bool DBG>
 static void launch_fused_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
                            uint32_t it_off, cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
-  launch_hi(rollout_kernel<SYS, BF16, DBG>, dim3(blocks), dim3(tile.block), 0, s, P, b.x0, b.U, b.it,
+  launch_hi(rollout_kernel<SYS, BF16, DBG>, dim3(blocks), dim3(tile.block), 0, s, true, P, b.x0, b.U, b.it,
             it_off, b.s_part, b.noise, b.rho_key, b.dbg_counts, b.dbg_J);
 }
 
@@ -350,7 +358,8 @@ cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const Roll
   if (tile.variant >= 2) {
     cudaError_t e = launch_noise(P, b, it_off, s);
     if (e != cudaSuccess) return e;
-    return launch_rollout_seq(P, b, tile, s);
+    // the rollout reads what the noise pass just wrote: an ordinary launch
+    return launch_rollout_seq(P, b, tile, false, s);
   }
   const bool dbg = b.dbg_counts != nullptr || b.dbg_J != nullptr;
   switch (P.system * 4 + (P.noise_bf16 ? 2 : 0) + (dbg ? 1 : 0)) {
@@ -368,7 +377,7 @@ cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const Roll
 
 template <bool BF16, int M, int VPT>
 static void launch_update_t(const UpdateArgs& a, const UpdateGeom& g, cudaStream_t s) {
-  launch_hi(update_kernel<BF16, M, VPT>, dim3(g.chunks, g.groups), dim3(kUpdateThreads), 0, s, a);
+  launch_hi(update_kernel<BF16, M, VPT>, dim3(g.chunks, g.groups), dim3(kUpdateThreads), 0, s, true, a);
 }
 
 template <bool BF16, int M>

@@ -40,6 +40,16 @@ __device__ __forceinline__ void publish_min_cost(float sk, uint32_t* rho_key) {
   if ((threadIdx.x & 31) == 0) atomicMin(rho_key, w);
 }
 
+// Programmatic dependent launch: a kernel launched as the programmatic
+// dependent of the previous kernel in its stream may start while that kernel
+// still runs; griddep_wait() returns once the previous kernel has completed
+// and its memory is visible (at once when there is no such dependency), and
+// griddep_launch_dependents() lets the next kernel start launching.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Mark of the nj-th jump of step j (stream 2+nj of the Philox counter) added
 // to J.
 __device__ __forceinline__ void add_mark(const DevProblem& P, uint32_t k, uint32_t j, uint32_t it,
@@ -199,6 +209,8 @@ rollout_kernel(const DevProblem P, const float* __restrict__ x0, const float* __
                void* __restrict__ noise,
                uint32_t* __restrict__ rho_key, uint8_t* __restrict__ dbg_counts,
                float* __restrict__ dbg_J) {
+  griddep_launch_dependents();
+  griddep_wait();  // U and the running minimum come from the previous update
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P.Kpad) return;
   fused_rollout_thread<SYS, BF16, DBG, false>(P, x0, U, __ldg(it_ptr) + it_off, k, s_part, noise,
@@ -374,6 +386,8 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
                      const float4* __restrict__ jrec, float* __restrict__ s_part,
                      uint32_t* __restrict__ rho_key) {
   constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
+  griddep_launch_dependents();
+  griddep_wait();  // U and the running minimum come from the previous update
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P.Kpad) return;  // whole warps: Kpad is a multiple of 32
   const bool active = k < P.K;
@@ -540,6 +554,7 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
   const int n_stages = (T + S - 1) / S;
   const int compute_warps = nt / 32;
 
+  griddep_launch_dependents();
   if (tid == nt) {
     mbar_init(full, 1);
     mbar_init(full + 1, 1);
@@ -556,7 +571,7 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
     const uint32_t d_bytes = (uint32_t)nk * m * SB, j_bytes = sj ? (uint32_t)nk * 16u : 0u,
                    c_bytes = (sj && q4) ? (uint32_t)nk : 0u;
     int issued = 0;
-    bool ok = true;
+    bool ok = true, waited = false;
     for (int st = 0; st < n_stages && ok; ++st) {
       const int buf = st & 1;
       if (st >= 2) {
@@ -570,7 +585,6 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
       unsigned char* base = stage_smem + buf * stage_bytes;
       const uint32_t u_bytes = ((uint32_t)ns * m * 4 + 15) & ~15u;
       mbar_expect_tx(full + buf, (uint32_t)ns * (d_bytes + j_bytes + c_bytes) + u_bytes);
-      bulk_load(base + u_off, U + (size_t)j0 * m, u_bytes, full + buf);
       for (int jj = 0; jj < ns; ++jj) {
         const size_t row = (size_t)(j0 + jj) * P.Kpad + k0;
         bulk_load(base + jj * d_stride, static_cast<const unsigned char*>(noise) + row * m * SB, d_bytes,
@@ -579,6 +593,13 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
         if (c_bytes)
           bulk_load(base + S * (d_stride + j_stride) + jj * c_stride, counts + row, c_bytes, full + buf);
       }
+      // the step data was drawn before the previous kernel; the controls come
+      // from the previous update
+      if (!waited) {
+        griddep_wait();
+        waited = true;
+      }
+      bulk_load(base + u_off, U + (size_t)j0 * m, u_bytes, full + buf);
       ++issued;
     }
     if (!ok) atomicExch(status, kStatusTimeout);
@@ -649,6 +670,7 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(empty + buf);
   }
+  griddep_wait();  // the running minimum was re-armed by the previous update
   if (mine) finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
 }
 
@@ -1046,8 +1068,15 @@ __device__ __forceinline__ void update_final_body(const UpdateArgs& a, bool ok, 
 template <bool BF16, int M, int VPT>
 __global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateArgs a) {
   __shared__ UpdateShared<kUpdateThreads, chunk_rollouts<BF16, M, VPT, kUpdateThreads>()> sh;
+  griddep_launch_dependents();
+  // Nothing before this wait may write global memory: with programmatic
+  // launches the next rollout, and even the next update, can start while
+  // this kernel's predecessors still run.  After it, the rollout (and so the
+  // previous update) has completed.
+  griddep_wait();
   // the next iteration's running minimum: its last reader (the previous
-  // update) has finished, and its next writer (the next rollout) has not begun
+  // update) has finished, and its next writer (the next rollout) writes it
+  // only after this kernel has completed
   if (a.rho_key_next && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     *a.rho_key_next = kKeyEmpty;
   const uint32_t key = __ldcg(a.rho_key);

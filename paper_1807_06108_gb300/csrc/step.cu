@@ -64,7 +64,9 @@ mppi_status capture_step(mppi_jump_ctx* ctx, int iters, cudaGraphExec_t* exec) {
       }
       if (e == cudaSuccess) e = cudaStreamWaitEvent(main, evN[r], 0);
       mark(3 * r);
-      if (e == cudaSuccess) e = launch_rollout_seq(ctx->P, b, ctx->tile, main);
+      // the noise arrives through an event (an ordinary dependency); the
+      // kernel before it in this stream is the previous update
+      if (e == cudaSuccess) e = launch_rollout_seq(ctx->P, b, ctx->tile, true, main);
     } else {
       mark(3 * r);
       if (e == cudaSuccess) e = launch_rollout(ctx->P, b, ctx->tile, (uint32_t)r, false, main);
