@@ -63,7 +63,10 @@ L2_BYTES = 129 * 1024 * 1024
 # profiles/quadrotor_K65536_T200_it5_bf16_kernels.md); None where no capture
 # of the current kernel exists.
 NCU_TRAFFIC = {
-    ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105189888 + 3017984,
+    ("quadrotor_K4096_T100_it10", "rollout_staged_kernel"): 13139200 + 0,
+    ("quadrotor_K4096_T100_it10", "update_kernel"): 6629888 + 0,
+    ("quadrotor_K65536_T200_it5_bf16", "rollout_staged_kernel"): 314624768 + 3227136,
+    ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105190656 + 3077888,
 }
 
 VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged", 4: "async"}
@@ -469,7 +472,7 @@ def run_ours(args):
     extras = {}
     if not args.no_extras:
         extras["batched"] = bench_batched()
-        extras["served"] = bench_served()
+        extras["served"] = bench_served(duration_s=args.served_seconds)
     line = {
         "metric": METRIC,
         "value": value,
@@ -532,6 +535,9 @@ def main():
                     help="time the rollout tile the library's autotuner picks")
     ap.add_argument("--tile", default="",
                     help="rollout tile 'variant,block,chunk' (1 fused, 2 split, 3 staged)")
+    ap.add_argument("--served-seconds", type=float, default=3.0,
+                    help="length of the served leg's Poisson arrival trace (the workload "
+                         "description's full trace is 60 s)")
     ap.add_argument("--only", choices=["batched", "served"],
                     help="run only the batched or served measurement (for profiling)")
     args = ap.parse_args()
@@ -539,7 +545,7 @@ def main():
     if args.only:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        res = bench_batched() if args.only == "batched" else bench_served()
+        res = bench_batched() if args.only == "batched" else bench_served(duration_s=args.served_seconds)
         print(json.dumps({args.only: res}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
