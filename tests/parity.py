@@ -25,10 +25,12 @@ U_RTOL = 1e-4
 NOISE_RTOL = 2e-6
 
 
-def gpu_iteration(prob, x0, U, it, debug=True):
+def gpu_iteration(prob, x0, U, it, debug=True, tile=None):
     from paper_1807_06108_gb300 import mppi
     s = mppi.Solver(prob)
     try:
+        if tile:
+            mppi.mppi_jump_set_tuning(s.ctx, *tile)
         s.set_controls(U)
         s.set_iteration(it)
         if debug:
@@ -152,8 +154,8 @@ def compare_iteration(prob, U_in, g, r, kc=None, check_update=True):
     return report
 
 
-def run_and_compare(prob, x0, U, it, kc=None):
-    g = gpu_iteration(prob, x0, U, it)
+def run_and_compare(prob, x0, U, it, kc=None, tile=None):
+    g = gpu_iteration(prob, x0, U, it, tile=tile)
     r = oracle_iteration(prob, x0, U, it, kc)
     rep = compare_iteration(prob, U, g, r, kc)
     assert g["it"] == it + 1

@@ -80,6 +80,16 @@ def test_iteration_matches_oracle(cuda, name):
     _record(name, rep)
 
 
+@pytest.mark.parametrize("tile", [(1, 64, 4), (2, 96, 8), (3, 32, 4)],
+                         ids=["fused", "split", "staged_small_blocks"])
+def test_other_rollout_tiles_match_oracle(cuda, tile):
+    """Non-default launch shapes against the oracle directly (they are also
+    compared bit for bit with one another in test_gpu_api)."""
+    prob, x0, U, it = CASES["quadrotor_laplace_bf16_sqrtdt"]
+    rep = parity.run_and_compare(prob, x0, U, it, tile=tile)
+    _record(f"quadrotor_laplace_bf16_sqrtdt_tile{tile}", rep)
+
+
 def test_large_quadrotor_sampled_and_full_update(cuda):
     """K=65536, T=200, dt=0.005, Laplace marks at 5/s, bfloat16 noise: every
     rollout's counts and noise, costs of rollouts 0..1023 and the full update
