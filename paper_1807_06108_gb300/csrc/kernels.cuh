@@ -1,10 +1,13 @@
 // kernels.cuh -- the kernels of one MPPI iteration on jump diffusions:
-//   rollout_kernel        fused sampling + rollout + augmented cost (A1+A2)
-//   noise_kernel          split form, part 1: sampling over K x T/4 threads (A1)
-//   rollout_split_kernel  split form, part 2: sequential rollout + cost (A2)
-//   update_kernel         free-energy weights, split-K weighted sum, combine,
-//                         U update, counter and MPC shift (A3+A4+A5)
-// Both rollout forms publish min_k S~_k through one atomic per warp.  The
+//   rollout_kernel         fused sampling + rollout + augmented cost (A1+A2)
+//   noise_kernel           split form, part 1: sampling over K x T/4 threads (A1)
+//   rollout_split_kernel   split form, part 2: sequential rollout + cost (A2),
+//                          step data through a register ring
+//   rollout_staged_kernel  split form, part 2 (the default): step data moved
+//                          into shared memory by a producer warp's bulk copies
+//   update_kernel          free-energy weights, split-K weighted sum, combine,
+//                          U update, counter and MPC shift (A3+A4+A5)
+// Every rollout form publishes min_k S~_k through one atomic per warp.  The
 // random stream of an iteration is selected by *it_ptr + it_off, so the noise
 // of a later iteration can be drawn while the current one is still rolled out.
 // Included by the translation units that launch them.
