@@ -67,8 +67,10 @@ def test_invalid_tile_rejected(cuda):
         s.close()
 
 
-@pytest.mark.parametrize("prob", [W.cartpole_k1000(), W.quadrotor_k4096(K=1024, T=60, iters=4)],
-                         ids=["cartpole_K1000_T50", "quadrotor_K1024_T60_it4"])
+@pytest.mark.parametrize("prob", [W.cartpole_k1000(), W.quadrotor_k4096(K=1024, T=60, iters=4),
+                                  W.large_quadrotor()],
+                         ids=["cartpole_K1000_T50", "quadrotor_K1024_T60_it4",
+                              "quadrotor_K65536_T200_it5_bf16_streaming_update"])
 def test_graph_step_equals_direct_calls_and_oracle(cuda, prob):
     x0 = W.initial_state(prob)
     iters = prob["iters"]
