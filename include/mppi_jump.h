@@ -104,7 +104,8 @@ typedef struct {
   uint64_t seed;         /* Philox key: (seed mod 2^32, seed >> 32) */
   mppi_cartpole_params cartpole;
   mppi_quadrotor_params quadrotor;
-  int32_t reserved;      /* must be 0 */
+  float alpha_decay;     /* step size alpha^r = alpha * alpha_decay^r at iteration r
+                            of an MPC step (Eq. 48-49); in [0, 1], 0 reads as 1 */
 } mppi_jump_config;
 
 typedef struct mppi_jump_ctx mppi_jump_ctx;
@@ -164,9 +165,9 @@ mppi_status mppi_jump_get_iteration(mppi_jump_ctx* ctx, uint32_t* it_host);
 mppi_status mppi_jump_rollout_cost(mppi_jump_ctx* ctx, const float* x0, float* costs);
 
 /* A3+A4 (Eq. 36-37, 49): softmin weights of the last rollout_cost and the
- * in-place update of the context's U, then counter += 1.  If every cost was
- * non-finite, U is left unchanged and the next synchronising call returns
- * MPPI_ENONFINITE. */
+ * in-place update of the context's U with step size alpha (the schedule's
+ * first step), then counter += 1.  If every cost was non-finite, U is left
+ * unchanged and the next synchronising call returns MPPI_ENONFINITE. */
 mppi_status mppi_jump_update(mppi_jump_ctx* ctx);
 
 /* A5 (Algorithm 1 MPC loop): `iters` x (rollout_cost + update) from the same

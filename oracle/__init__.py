@@ -75,6 +75,7 @@ class _Problem(ctypes.Structure):
         ("qr_weta", ctypes.c_double), ("qr_wom", ctypes.c_double),
         ("qr_obs", ctypes.c_double * 3), ("qr_obs_r", ctypes.c_double),
         ("qr_obs_cost", ctypes.c_double),
+        ("alpha_decay", ctypes.c_double),
     ]
 
 
@@ -147,6 +148,7 @@ def make_problem(prob):
     P.system = 0 if prob["system"] == "cartpole" else 1
     P.K, P.T = prob["K"], prob["T"]
     P.dt, P.lam, P.c, P.alpha = prob["dt"], prob["lam"], prob["c"], prob["alpha"]
+    P.alpha_decay = prob.get("alpha_decay", 1.0)
     for i, s in enumerate(prob["sigma"]):
         P.sigma[i] = s
     P.nu = prob["nu"]

@@ -76,6 +76,9 @@ typedef struct {
   /* quadrotor */
   double qr_mass, qr_J[3], qr_arm, qr_kappa, qr_g, qr_goal[3];
   double qr_wp, qr_wv, qr_weta, qr_wom, qr_obs[3], qr_obs_r, qr_obs_cost;
+  /* step sizes alpha^r = alpha * alpha_decay^r over the iterations r of one
+   * MPC step (Eq. 48-49); 1 keeps alpha constant */
+  double alpha_decay;
 } orc_problem;
 
 int orc_state_dim(const orc_problem* P) { return P->system == 0 ? 4 : 12; }
@@ -537,14 +540,18 @@ int orc_iteration(const orc_problem* P, const double* x0, double* U, uint32_t it
 }
 
 /* One MPC step of Algorithm 1: `iters` iterations starting at counter it0
- * from the same x0, then execute u_0 (returned in u0_out), shift the
- * sequence by one step and append u_init. */
+ * from the same x0, iteration r with the step size alpha^r = alpha *
+ * alpha_decay^r of the stochastic-optimisation update (Eq. 48-49), then
+ * execute u_0 (returned in u0_out), shift the sequence by one step and append
+ * u_init. */
 int orc_step(const orc_problem* P, const double* x0, double* U, uint32_t it0, int32_t iters,
              double* u0_out, int32_t nthreads) {
   const int T = P->T, m = orc_control_dim(P);
   if (iters < 1) return ORC_EINVAL;
+  orc_problem Pr = *P;
   for (int r = 0; r < iters; ++r) {
-    int st = orc_iteration(P, x0, U, it0 + (uint32_t)r, NULL, NULL, NULL, NULL, NULL, NULL,
+    Pr.alpha = P->alpha * pow(P->alpha_decay, (double)r);
+    int st = orc_iteration(&Pr, x0, U, it0 + (uint32_t)r, NULL, NULL, NULL, NULL, NULL, NULL,
                            nthreads);
     if (st) return st;
   }

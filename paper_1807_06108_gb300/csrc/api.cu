@@ -124,6 +124,7 @@ mppi_status mppi_jump_default_config(int32_t system, mppi_jump_config* out) {
   out->lambda = 1.0f;
   out->c = 1.0f;
   out->alpha = 1.0f;
+  out->alpha_decay = 1.0f;
   out->count_law = MPPI_COUNT_POISSON;
   out->mark_law = MPPI_MARK_NORMAL;
   out->jump_channel = MPPI_JUMP_STATE;
@@ -218,7 +219,6 @@ mppi_status mppi_jump_init(const mppi_jump_config* cfg, void* stream, mppi_jump_
     return st;
   }
   ctx->cfg = *cfg;
-  ctx->cfg.reserved = 0;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = prepare_kernels();
   if (e == cudaSuccess) {
@@ -416,7 +416,6 @@ mppi_status mppi_jump_set_state(mppi_jump_ctx* ctx, const void* buf_host, size_t
   p += sizeof(hdr);
   mppi_jump_config cfg;
   std::memcpy(&cfg, p, sizeof(cfg));
-  cfg.reserved = 0;
   if (std::memcmp(&cfg, &ctx->cfg, sizeof(cfg)) != 0)
     return fail(ctx->err, MPPI_EINVAL, "checkpoint was taken with another configuration");
   p += sizeof(cfg);

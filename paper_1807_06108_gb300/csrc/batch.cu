@@ -121,7 +121,7 @@ __device__ __forceinline__ UpdateArgs update_args(const BatchInst& I, int r) {
   u.rows = I.rows;
   u.inv_lam = P.inv_lam;
   u.lam = P.lam;
-  u.alpha = P.alpha;
+  u.alpha = P.alpha * powf(P.alpha_decay, (float)r);
   for (int i = 0; i < 4; ++i) {
     u.inv_sigma2[i] = P.inv_sigma2[i];
     u.u_init[i] = P.u_init[i];

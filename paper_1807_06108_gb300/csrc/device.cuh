@@ -31,6 +31,7 @@ struct DevProblem {
   uint32_t key0, key1;
   uint32_t thr[kMaxJumps];  // jump-count thresholds (see the header)
   float dt, lam, inv_lam, is_coef, alpha, s_jump;
+  float alpha_decay;  // step size alpha * alpha_decay^r at iteration r of a step
   float sqc_sigma[4];   // sqrt(c) * sigma_i
   float inv_sigma2[4];  // 1 / sigma_i^2
   float mark_scale[4];

@@ -87,10 +87,11 @@ cudaError_t launch_rollout_seq(const DevProblem& P, const IterBuffers& b, const 
 // iteration, so only a rollout that follows no update needs it).
 cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
                            uint32_t it_off, bool arm_min, cudaStream_t s);
-// Weights + update; shift != 0 performs the MPC shift and writes u0 (if not
+// Weights + update of iteration r of an MPC step (step size alpha *
+// alpha_decay^r); shift != 0 performs the MPC shift and writes u0 (if not
 // NULL); the counter advances by it_advance.
-cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g, int shift,
-                          uint32_t it_advance, float* u0, cudaStream_t s);
+cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g, int r,
+                          int shift, uint32_t it_advance, float* u0, cudaStream_t s);
 // costs[k] = S~_k (the full augmented cost) when b.costs is not NULL.
 cudaError_t launch_costs(const DevProblem& P, const IterBuffers& b, cudaStream_t s);
 // w_k = e_k / Z (Z = diag[1]) for the weights getter.

@@ -34,6 +34,8 @@ mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg) 
   if (!finite_pos(cfg->lambda)) return fail(msg, MPPI_EINVAL, "lambda must be finite and > 0");
   if (!finite_pos(cfg->c)) return fail(msg, MPPI_EINVAL, "c must be finite and > 0");
   if (!std::isfinite(cfg->alpha)) return fail(msg, MPPI_EINVAL, "alpha must be finite");
+  if (!(cfg->alpha_decay >= 0.0f && cfg->alpha_decay <= 1.0f))
+    return fail(msg, MPPI_EINVAL, "alpha_decay must be in [0, 1]");
   for (int i = 0; i < m; ++i)
     if (!finite_pos(cfg->sigma[i])) return fail(msg, MPPI_EINVAL, "sigma[%d] must be finite and > 0", i);
   if (cfg->count_law != MPPI_COUNT_POISSON && cfg->count_law != MPPI_COUNT_BERNOULLI)
@@ -92,6 +94,7 @@ mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg) 
   P->inv_lam = (float)(1.0 / (double)cfg->lambda);
   P->is_coef = (float)(0.5 * (1.0 - 1.0 / (double)cfg->c));
   P->alpha = cfg->alpha;
+  P->alpha_decay = cfg->alpha_decay == 0.0f ? 1.0f : cfg->alpha_decay;
   P->s_jump = cfg->jump_sqrt_dt ? (float)std::sqrt((double)cfg->dt) : 1.0f;
   const double sqc = std::sqrt((double)cfg->c);
   for (int i = 0; i < 4; ++i) {
@@ -387,7 +390,7 @@ static void launch_update_m(const UpdateArgs& a, const UpdateGeom& g, cudaStream
   else launch_update_t<BF16, M, 1>(a, g, s);
 }
 
-cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g, int shift,
+cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g, int r, int shift,
                           uint32_t it_advance, float* u0, cudaStream_t s) {
   UpdateArgs a;
   a.noise = b.noise;
@@ -398,7 +401,7 @@ cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const Updat
   a.rows = g.rows;
   a.inv_lam = P.inv_lam;
   a.lam = P.lam;
-  a.alpha = P.alpha;
+  a.alpha = (float)((double)P.alpha * std::pow((double)P.alpha_decay, (double)r));
   for (int i = 0; i < 4; ++i) a.inv_sigma2[i] = P.inv_sigma2[i];
   a.chunks = g.chunks;
   a.groups = g.groups;

@@ -74,7 +74,7 @@ mppi_status capture_step(mppi_jump_ctx* ctx, int iters, cudaGraphExec_t* exec) {
     }
     mark(3 * r + 1);
     if (e == cudaSuccess)
-      e = launch_update(ctx->P, b, ctx->geom, last ? 1 : 0, last ? (uint32_t)iters : 0u,
+      e = launch_update(ctx->P, b, ctx->geom, r, last ? 1 : 0, last ? (uint32_t)iters : 0u,
                         last ? ctx->u0 : nullptr, main);
     mark(3 * r + 2);
     if (split && e == cudaSuccess) e = cudaEventRecord(evU[r], main);
@@ -120,7 +120,7 @@ mppi_status mppi_jump_rollout_cost(mppi_jump_ctx* ctx, const float* x0, float* c
 
 mppi_status mppi_jump_update(mppi_jump_ctx* ctx) {
   if (!ctx) return MPPI_EINVAL;
-  CK(launch_update(ctx->P, ctx_buffers(ctx, nullptr, 0), ctx->geom, 0, 1u, nullptr, ctx->stream),
+  CK(launch_update(ctx->P, ctx_buffers(ctx, nullptr, 0), ctx->geom, 0, 0, 1u, nullptr, ctx->stream),
      "update launch");
   return MPPI_OK;
 }

@@ -72,7 +72,7 @@ class Config(ctypes.Structure):
         ("jump_rows", ctypes.c_int32 * 4), ("jump_sqrt_dt", ctypes.c_int32),
         ("noise_dtype", ctypes.c_int32), ("u_init", ctypes.c_float * 4),
         ("seed", ctypes.c_uint64), ("cartpole", CartpoleParams),
-        ("quadrotor", QuadrotorParams), ("reserved", ctypes.c_int32),
+        ("quadrotor", QuadrotorParams), ("alpha_decay", ctypes.c_float),
     ]
 
 
@@ -299,6 +299,7 @@ def config_from_problem(prob):
     cfg.system = 0 if prob["system"] == "cartpole" else 1
     cfg.K, cfg.T = prob["K"], prob["T"]
     cfg.dt, cfg.lam, cfg.c, cfg.alpha = prob["dt"], prob["lam"], prob["c"], prob["alpha"]
+    cfg.alpha_decay = prob.get("alpha_decay", 1.0)
     for i, s in enumerate(prob["sigma"]):
         cfg.sigma[i] = s
     cfg.jump_rate = prob["nu"]

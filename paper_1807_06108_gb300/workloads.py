@@ -71,7 +71,7 @@ def _canon_params(system, params):
 
 def problem(system, K, T, dt, *, sigma, nu, mark_scale, mark_law="normal",
             count_law="poisson", jump_channel="state", jump_rows=None, lam=1.0,
-            c=1.0, alpha=1.0, noise_dtype="f32", seed=0, jump_sqrt_dt=False,
+            c=1.0, alpha=1.0, alpha_decay=1.0, noise_dtype="f32", seed=0, jump_sqrt_dt=False,
             params=None, u_init=None, iters=1, name=None):
     """Build one problem dictionary (all floats float32-representable)."""
     if system not in SYSTEMS:
@@ -102,6 +102,7 @@ def problem(system, K, T, dt, *, sigma, nu, mark_scale, mark_law="normal",
         "lam": f32(lam),
         "c": f32(c),
         "alpha": f32(alpha),
+        "alpha_decay": f32(alpha_decay),
         "sigma": f32(list(sigma)),
         "nu": f32(nu),
         "count_law": count_law,

@@ -105,6 +105,29 @@ def test_graph_step_equals_direct_calls_and_oracle(cuda, prob):
     assert err <= 1e-4 * iters
 
 
+@pytest.mark.parametrize("prob", [
+    W.quadrotor_k4096(K=1024, T=60, iters=4, alpha_decay=0.6),
+    W.cartpole_k1000(K=500, T=30, iters=3, alpha=0.7, alpha_decay=0.5),
+], ids=["quadrotor_decay06", "cartpole_alpha07_decay05"])
+def test_step_size_schedule_matches_oracle(cuda, prob):
+    """alpha^r = alpha * alpha_decay^r over the iterations of one MPC step
+    (Eq. 48-49): the graph-replayed step against the oracle's Algorithm-1
+    step with the same schedule."""
+    x0 = W.initial_state(prob)
+    iters = prob["iters"]
+    s = _solver(prob)
+    try:
+        u0 = s.step(x0)
+        U_step = s.controls()
+    finally:
+        s.close()
+    u0_ref, U_ref = oracle.step(prob, x0, W.initial_controls(prob), 0, iters)
+    dU_ref = U_ref[:-1] - W.initial_controls(prob)[1:]
+    den = max(np.max(np.abs(dU_ref)), np.max(np.abs(u0_ref - prob["u_init"])), 1e-30)
+    err = max(np.max(np.abs(U_step[:-1] - U_ref[:-1])), np.max(np.abs(u0 - u0_ref))) / den
+    assert err <= 1e-4 * iters, err
+
+
 def test_checkpoint_restore_continues_stream(cuda):
     prob = W.quadrotor_k4096(K=512, T=30, iters=3)
     x0 = W.initial_state(prob)

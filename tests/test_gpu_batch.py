@@ -24,6 +24,8 @@ def _mixed(noise_dtype):
         W.quadrotor_k4096(K=96, T=64, seed=15, noise_dtype=noise_dtype, iters=2,
                           jump_channel="control", mark_scale=0.3, lam=30.0),
         W.cartpole_k1000(K=33, T=5, seed=16, noise_dtype=noise_dtype, iters=4),
+        W.quadrotor_k4096(K=256, T=31, seed=17, noise_dtype=noise_dtype, iters=3, lam=20.0,
+                          alpha_decay=0.6),
     ]
 
 

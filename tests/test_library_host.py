@@ -97,6 +97,7 @@ def test_validation_rejects_bad_configs(lib):
         ("K", 0), ("T", 0), ("T", 5000), ("dt", 0.0), ("dt", float("nan")), ("lam", -1.0),
         ("c", 0.0), ("jump_rate", -1.0), ("jump_rate", 1e6), ("count_law", 7), ("mark_law", 3),
         ("jump_channel", 2), ("noise_dtype", 9), ("q", 5), ("system", 4),
+        ("alpha_decay", 1.5), ("alpha_decay", -0.1), ("alpha_decay", float("nan")),
     ]
     for field, val in bad_edits:
         cfg = lib.config_from_problem(W.quadrotor_k4096())

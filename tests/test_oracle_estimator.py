@@ -222,6 +222,27 @@ def test_step_executes_first_control_and_shifts():
     np.testing.assert_array_equal(Us[-1], prob["u_init"])
 
 
+def test_step_size_schedule_of_the_stochastic_optimisation_update():
+    """Eq. 48-49 take a step size alpha^k per iteration; with alpha_decay = d
+    iteration r of a step uses alpha * d^r, which is the plain iteration with
+    that alpha (and d = 1 is the constant step of Eq. 36)."""
+    base = W.quadrotor_k4096(K=150, T=6, iters=4, alpha=0.8)
+    prob = dict(base, alpha_decay=0.5)
+    rng = np.random.default_rng(9)
+    x0, U = W.random_state(prob, rng), W.random_controls(prob, rng)
+    Uo = U.astype(np.float64)
+    for r in range(4):
+        Uo = oracle.iteration(dict(prob, alpha=prob["alpha"] * 0.5 ** r), x0, Uo, 11 + r)["U"]
+    u0, Us = oracle.step(prob, x0, U, 11, 4)
+    np.testing.assert_allclose(u0, Uo[0], rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(Us[:-1], Uo[1:], rtol=1e-15, atol=1e-15)
+    u0c, Usc = oracle.step(dict(base, alpha_decay=1.0), x0, U, 11, 4)
+    u0b, Usb = oracle.step(base, x0, U, 11, 4)
+    np.testing.assert_array_equal(Usc, Usb)
+    # a smaller schedule moves the controls less from the first iteration on
+    assert not np.allclose(Us, Usb)
+
+
 def test_iterations_use_fresh_counters():
     prob = W.cartpole_k1000(K=50, T=5)
     x0, U = W.initial_state(prob), W.initial_controls(prob)
