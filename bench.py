@@ -44,6 +44,7 @@ WORKLOADS = {
     "quadrotor_k4096": W.quadrotor_k4096,
     "cartpole_k1000": W.cartpole_k1000,
     "large_quadrotor": W.large_quadrotor,
+    "quadrotor_alg1": W.quadrotor_alg1,
 }
 METRIC = "trajectory-steps/s (MPC solves of MPPI on jump diffusions)"
 

@@ -173,6 +173,18 @@ def quadrotor_k4096(K=4096, T=100, dt=0.01, **kw):
     return problem("quadrotor", K, T, dt, **args)
 
 
+def quadrotor_alg1(K=4096, T=100, dt=0.01, **kw):
+    """The quadrotor workload in Algorithm 1's literal form: jumps enter the
+    control channels (H = G, q = m) with the zero-one jump timer, the step
+    size decays over the iterations (alpha^k of Eq. 48-49, alpha_decay 0.8);
+    otherwise as quadrotor_k4096."""
+    args = dict(sigma=0.2, nu=2.0, mark_scale=0.5, lam=1.0, seed=0, iters=10,
+                jump_channel="control", count_law="bernoulli", alpha_decay=0.8,
+                name=f"quadrotor_K{K}_T{T}_alg1")
+    args.update(kw)
+    return problem("quadrotor", K, T, dt, **args)
+
+
 def large_quadrotor(K=65536, T=200, dt=0.005, **kw):
     """Large quadrotor: K=65536, T=200 steps of 0.005 s, 5 iterations,
     Laplace(0, 1.0) velocity-jump marks at 5.0/s, bfloat16 noise storage."""

@@ -65,6 +65,9 @@ def _cases():
     p = W.quadrotor_k4096(K=515, T=27, nu=12.0, jump_rows=[3, 4, 5, 9], mark_scale=0.5)
     r = rng(7)
     c["quadrotor_q4_state_rows"] = (p, W.random_state(p, r, 0.1), W.random_controls(p, r, 0.2), 6)
+    p = W.quadrotor_alg1()
+    r = rng(8)
+    c["quadrotor_alg1_K4096_T100"] = (p, W.random_state(p, r, 0.1), W.random_controls(p, r, 0.2), 12)
     p = W.cartpole_k1000(K=5000, T=50, nu=0.0)
     c["cartpole_no_jumps"] = (p, W.initial_state(p), W.initial_controls(p), 4)
     return c
