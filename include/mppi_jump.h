@@ -22,8 +22,9 @@
  *     synchronise that stream before returning.
  *   - Errors are returned as mppi_status codes; nothing aborts, traps or
  *     throws.  mppi_jump_last_error() gives a message for the last failure on
- *     a context.  Device-side conditions (all costs non-finite) are recorded
- *     in a status word that the next synchronising call returns.
+ *     a context.  Device-side conditions (all costs non-finite: MPPI_ENONFINITE;
+ *     a bounded device wait that expired: MPPI_ETIMEOUT) are recorded in a
+ *     status word that the next synchronising call returns.
  *   - A context is not thread-safe; distinct contexts are independent.
  *   - All arrays are dense, row-major, float32 unless stated:
  *       x0 [n], U [T][m], costs [K], weights [K],
@@ -171,8 +172,9 @@ mppi_status mppi_jump_rollout_cost(mppi_jump_ctx* ctx, const float* x0, float* c
 mppi_status mppi_jump_update(mppi_jump_ctx* ctx);
 
 /* A5 (Algorithm 1 MPC loop): `iters` x (rollout_cost + update) from the same
- * x0, then u0 = U_0, U_i <- U_{i+1}, U_{T-1} <- u_init.  The work is replayed
- * from a CUDA graph captured on first use for each `iters`.
+ * x0, iteration r with step size alpha * alpha_decay^r, then u0 = U_0,
+ * U_i <- U_{i+1}, U_{T-1} <- u_init.  The work is replayed from a CUDA graph
+ * captured on first use for each `iters`.
  * mppi_jump_step takes HOST x0 [n] and writes HOST u0 [m] (synchronous);
  * mppi_jump_step_async takes device pointers and does not synchronise. */
 mppi_status mppi_jump_step(mppi_jump_ctx* ctx, const float* x0_host, int32_t iters,
