@@ -653,7 +653,11 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
       float4 jr_n;
       int cnt_n;
       fetch(0, de_n, u_n, jr_n, cnt_n);
-#pragma unroll 2
+      // unrolled twice for long stages (one block per SM, latency-bound);
+      // not at all for short ones (several blocks per SM, issue-bound: the
+      // smaller loop body keeps more of it in the instruction cache)
+      constexpr int kUnroll = S >= 16 ? 2 : 1;
+#pragma unroll kUnroll
       for (int jj = 0; jj < ns; ++jj) {
         float de[m], u[m];
 #pragma unroll
