@@ -66,7 +66,6 @@ L2_BYTES = 129 * 1024 * 1024
 NCU_TRAFFIC = {
     ("quadrotor_K4096_T100_it10", "rollout_staged_kernel"): 13139200 + 0,
     ("quadrotor_K4096_T100_it10", "update_kernel"): 6629888 + 0,
-    ("quadrotor_K65536_T200_it5_bf16", "rollout_staged_kernel"): 314624768 + 3227136,
     ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105190656 + 3077888,
 }
 
