@@ -358,11 +358,7 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
                                  : make_float4(J[jj][0], J[jj][1], J[jj][2], (float)N[jj]);
       jrec[row] = active ? rec : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
-    if constexpr (BF16) {
-#pragma unroll
-      for (int i = 0; i < M; ++i) de[i] = __bfloat162float(__float2bfloat16_rn(de[i]));
-    }
-    store_noise<M, BF16>(noise, row, de, active);
+    store_noise<M, BF16>(noise, row, de, active);  // rounds to bfloat16 (RNE) when BF16
     counts[row] = active ? (uint8_t)N[jj] : (uint8_t)0;
     if (DBG && active) {
       const size_t rk = (size_t)j * P.K + k;
