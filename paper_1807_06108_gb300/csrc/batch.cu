@@ -213,10 +213,19 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
           const int j_begin = (int)w.b * I.rows;
           const int j_end = min(I.P.T, j_begin + I.rows);
           float* zdst = w.b == 0 ? u.zpart + w.a : nullptr;
-          if (I.P.m == 4)
-            update_partial_body<BF16, 4, kBatchVPT, NT>(u, rho, (int)w.a, j_begin, j_end, w.b == 0, zdst, sh4);
-          else
-            update_partial_body<BF16, 1, kBatchVPT, NT>(u, rho, (int)w.a, j_begin, j_end, w.b == 0, zdst, sh1);
+          if (I.P.m == 4) {
+            UpdatePrefetch<BF16, 4, kBatchVPT, NT> pf;
+            update_prefetch_noise<BF16, 4, kBatchVPT, NT>(u, (int)w.a, j_begin, j_end, pf);
+            update_prefetch_costs<BF16, 4, kBatchVPT, NT>(u, (int)w.a, pf);
+            update_partial_body<BF16, 4, kBatchVPT, NT>(u, rho, (int)w.a, j_begin, j_end, w.b == 0, zdst, pf,
+                                                        sh4);
+          } else {
+            UpdatePrefetch<BF16, 1, kBatchVPT, NT> pf;
+            update_prefetch_noise<BF16, 1, kBatchVPT, NT>(u, (int)w.a, j_begin, j_end, pf);
+            update_prefetch_costs<BF16, 1, kBatchVPT, NT>(u, (int)w.a, pf);
+            update_partial_body<BF16, 1, kBatchVPT, NT>(u, rho, (int)w.a, j_begin, j_end, w.b == 0, zdst, pf,
+                                                        sh1);
+          }
         }
         signal = I.done_W + r;
       } else {

@@ -89,7 +89,8 @@ cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const Roll
                            uint32_t it_off, bool arm_min, cudaStream_t s);
 // Weights + update of iteration r of an MPC step (step size alpha *
 // alpha_decay^r); shift != 0 performs the MPC shift and writes u0 (if not
-// NULL); the counter advances by it_advance.
+// NULL); the counter advances by it_advance.  An ordinary launch (it
+// starts once the preceding kernel has completed).
 cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g, int r,
                           int shift, uint32_t it_advance, float* u0, cudaStream_t s);
 // costs[k] = S~_k (the full augmented cost) when b.costs is not NULL.

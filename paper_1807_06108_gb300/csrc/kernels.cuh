@@ -795,10 +795,54 @@ struct UpdateArgs {
   float u_init[4];
 };
 
-template <bool BF16, int M, int VPT, int NT, class SH>
+// Loads of a partial body that do not depend on rho, issued early so that
+// their latency overlaps other work: the first batch of 16-byte vectors of
+// the warp's first row, and the chunk's first costs S~_k.
+template <bool BF16, int M, int VPT, int NT>
+struct UpdatePrefetch {
+  static constexpr int kB = 4;                                         // 16-byte loads per lane in flight
+  static constexpr int kWT = chunk_rollouts<BF16, M, VPT, NT>() / NT;  // costs per thread
+  static constexpr int kWB = kWT < 8 ? kWT : 8;                        // of them, loaded up front
+  uint4 q[kB];
+  float s[kWB];
+};
+
+template <bool BF16, int M, int VPT, int NT, class PF>
+__device__ __forceinline__ void update_prefetch_noise(const UpdateArgs& a, int chunk, int j_begin,
+                                                      int j_end, PF& pf) {
+  constexpr int E = BF16 ? 8 : 4;
+  constexpr int CV = NT * VPT;
+  const int lane = threadIdx.x & 31, j_first = j_begin + (threadIdx.x >> 5);
+  const int nvec = a.Kpad * M / E;
+  const int v0 = chunk * CV;
+  const int nvc = min(CV, nvec - v0);
+  if (j_first < j_end) {
+    const uint4* row = reinterpret_cast<const uint4*>(a.noise) + (size_t)j_first * nvec + v0;
+#pragma unroll
+    for (int h = 0; h < PF::kB; ++h) {
+      const int v = lane + 32 * h;
+      pf.q[h] = v < nvc ? __ldcs(row + v) : make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+}
+
+template <bool BF16, int M, int VPT, int NT, class PF>
+__device__ __forceinline__ void update_prefetch_costs(const UpdateArgs& a, int chunk, PF& pf) {
+  constexpr int RPV = (BF16 ? 8 : 4) / M;
+  constexpr int CV = NT * VPT;
+  const int v0 = chunk * CV;
+  const int nr = min(CV, a.Kpad * M / (BF16 ? 8 : 4) - v0) * RPV;  // rollouts of the chunk
+#pragma unroll
+  for (int t = 0; t < PF::kWB; ++t) {
+    const int r = threadIdx.x + t * NT;
+    pf.s[t] = r < nr ? __ldcg(a.s_part + v0 * RPV + r) : 0.0f;
+  }
+}
+
+template <bool BF16, int M, int VPT, int NT, class PF, class SH>
 __device__ __forceinline__ void update_partial_body(const UpdateArgs& a, float rho, int chunk,
                                                     int j_begin, int j_end, bool write_e, float* zdst,
-                                                    SH& sh) {
+                                                    PF& pf, SH& sh) {
   constexpr int E = BF16 ? 8 : 4;  // elements per 16-byte vector
   constexpr int RPV = E / M;       // rollouts per vector
   constexpr int W = NT / 32;
@@ -807,28 +851,26 @@ __device__ __forceinline__ void update_partial_body(const UpdateArgs& a, float r
   const int nvec = a.Kpad * M / E;
   const int v0 = chunk * CV;
   const int nvc = min(CV, nvec - v0);  // vectors of this chunk
-  constexpr int B = 4;                 // 16-byte loads in flight per lane
+  constexpr int B = PF::kB;            // 16-byte loads in flight per lane
   const uint4* nv = reinterpret_cast<const uint4*>(a.noise);
-  // the first loads of the warp's first row go out before the weights are
-  // formed (they do not depend on them), so their latency overlaps that phase
-  const int j_first = j_begin + wid;
-  uint4 q[B];
-  if (j_first < j_end) {
-    const uint4* row = nv + (size_t)j_first * nvec + v0;
-#pragma unroll
-    for (int h = 0; h < B; ++h) {
-      const int v = lane + 32 * h;
-      q[h] = v < nvc ? __ldcs(row + v) : make_uint4(0u, 0u, 0u, 0u);
-    }
-  }
-  // the chunk's weights, once, into shared memory
+  const int j_first = j_begin + wid;  // its first batch is in pf.q
+  uint4* q = pf.q;
+  // the chunk's weights, once, into shared memory (all loads of a thread
+  // are independent, so they are in flight together)
   float zs = 0.0f, zc = 0.0f;
-  for (int r = tid; r < nvc * RPV; r += NT) {
-    const int k = v0 * RPV + r;
-    const float e = expf((rho - __ldcg(a.s_part + k)) * a.inv_lam);
-    sh.e[r] = e;
-    if (write_e) a.e_out[k] = e;
-    two_sum_acc(zs, zc, e);
+  const int nr = nvc * RPV;
+#pragma unroll
+  for (int t = 0; t < PF::kWT; ++t) {
+    const int r = tid + t * NT;
+    float sv;
+    if (t < PF::kWB) sv = pf.s[t < PF::kWB ? t : 0];
+    else sv = r < nr ? __ldcg(a.s_part + v0 * RPV + r) : 0.0f;
+    if (r < nr) {
+      const float e = expf((rho - sv) * a.inv_lam);
+      sh.e[r] = e;
+      if (write_e) a.e_out[v0 * RPV + r] = e;
+      two_sum_acc(zs, zc, e);
+    }
   }
   if (zdst) {
     const float z = block_sum2<NT>(zs, zc, sh.sh_s, sh.sh_c);  // its barriers publish sh.e
@@ -1072,25 +1114,29 @@ template <bool BF16, int M, int VPT>
 __global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateArgs a) {
   __shared__ UpdateShared<kUpdateThreads, chunk_rollouts<BF16, M, VPT, kUpdateThreads>()> sh;
   griddep_launch_dependents();
-  // Nothing before this wait may write global memory: with programmatic
-  // launches the next rollout, and even the next update, can start while
-  // this kernel's predecessors still run.  After it, the rollout (and so the
-  // previous update) has completed.
+  const int g = blockIdx.y;
+  const int j_begin = g * a.rows;
+  const int j_end = min(a.T, j_begin + a.rows);
+  // The update is launched as an ordinary dependent of the rollout, so the
+  // wait returns at once; it keeps the kernel correct as a programmatic
+  // dependent too (nothing before it may write global memory).  The rollout
+  // of the next iteration is launched as a programmatic dependent of this
+  // kernel and waits for its completion before it writes anything.
   griddep_wait();
   // the next iteration's running minimum: its last reader (the previous
   // update) has finished, and its next writer (the next rollout) writes it
   // only after this kernel has completed
   if (a.rho_key_next && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     *a.rho_key_next = kKeyEmpty;
+  UpdatePrefetch<BF16, M, VPT, kUpdateThreads> pf;
+  update_prefetch_noise<BF16, M, VPT, kUpdateThreads>(a, blockIdx.x, j_begin, j_end, pf);
+  update_prefetch_costs<BF16, M, VPT, kUpdateThreads>(a, blockIdx.x, pf);
   const uint32_t key = __ldcg(a.rho_key);
   const bool ok = key < kKeyInf;  // at least one finite cost
   const float rho = ok ? key_to_float(key) : 0.0f;
-  const int g = blockIdx.y;
   if (ok) {
-    const int j_begin = g * a.rows;
-    const int j_end = min(a.T, j_begin + a.rows);
     update_partial_body<BF16, M, VPT, kUpdateThreads>(
-        a, rho, blockIdx.x, j_begin, j_end, g == 0, a.zpart + (size_t)g * a.chunks + blockIdx.x, sh);
+        a, rho, blockIdx.x, j_begin, j_end, g == 0, a.zpart + (size_t)g * a.chunks + blockIdx.x, pf, sh);
   }
   // the barrier orders the block's stores before thread 0's fence and
   // ticket; each winner fences again before reading what the others wrote

@@ -6,9 +6,10 @@
 // branches: with the split or staged rollout tiles, the noise of iteration
 // r+1 is drawn on the second branch (into the other buffer set) while
 // iteration r is rolled out and updated on the first, so the sampling costs
-// no time on the critical path; on the first branch each kernel is a
-// programmatic dependent of the one before it.  Iteration r of a step uses the Philox stream of counter
-// value it + r; the last update advances the counter by the iteration count.
+// no time on the critical path; on the first branch each rollout is a
+// programmatic dependent of the update before it.  Iteration r of a step uses
+// the Philox stream of counter value it + r; the last update advances the
+// counter by the iteration count.
 #include <cstring>
 #include <vector>
 
