@@ -64,9 +64,10 @@ L2_BYTES = 129 * 1024 * 1024
 # profiles/quadrotor_K65536_T200_it5_bf16_kernels.md); None where no capture
 # of the current kernel exists.
 NCU_TRAFFIC = {
-    ("quadrotor_K4096_T100_it10", "rollout_staged_kernel"): 13139200 + 0,
-    ("quadrotor_K4096_T100_it10", "update_kernel"): 6629888 + 0,
-    ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105190656 + 3077888,
+    ("quadrotor_K4096_T100_it10", "rollout_staged_kernel"): 13138688 + 0,
+    ("quadrotor_K4096_T100_it10", "update_kernel"): 6629632 + 0,
+    ("quadrotor_K65536_T200_it5_bf16", "rollout_staged_kernel"): 314648064 + 4102144,
+    ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105188352 + 2928128,
 }
 
 VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged", 4: "async"}

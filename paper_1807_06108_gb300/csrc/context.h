@@ -57,7 +57,6 @@ namespace mj {
 mppi_status cuda_fail(mppi_jump_ctx* ctx, cudaError_t e, const char* what);
 IterBuffers ctx_buffers(mppi_jump_ctx* ctx, float* costs, int set);
 void drop_graphs(mppi_jump_ctx* ctx);
-int num_sms_of_current();
 
 }  // namespace mj
 

@@ -20,6 +20,9 @@ mppi_status fail(char* buf, mppi_status st, const char* fmt, ...);
 // reciprocals, Philox key).  msg receives a reason on failure.
 mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg);
 
+// SMs of the current device.
+int num_sms_of_current();
+
 inline int state_dim(int system) { return system == MPPI_CARTPOLE ? 4 : 12; }
 inline int control_dim(int system) { return system == MPPI_CARTPOLE ? 1 : 4; }
 inline int pad_k(int K) { return (K + 31) / 32 * 32; }

@@ -244,10 +244,9 @@ static void launch_hi(void (*kernel)(Params...), dim3 grid, dim3 block, size_t s
 
 // Measured on GB300: the staged form (a producer warp moves the step data
 // into shared memory with bulk copies) is the fastest rollout at every size;
-// while the rollout blocks fit on the SMs about once, 16-step stages (about
-// 130 KB of shared memory per block, which also keeps the concurrent noise
-// pass off the rollout's SMs), beyond that 8-step stages so that several
-// blocks share an SM.
+// while the rollout blocks fit on the SMs about once, 16-step stages (one
+// block per SM, see launch_staged_t), beyond that 8-step stages so that
+// several blocks share an SM.
 RolloutTile default_tile(const DevProblem& P, int num_sms) {
   const int sms = num_sms > 0 ? num_sms : 152;
   const int blocks = (P.Kpad + 127) / 128;
@@ -307,8 +306,15 @@ template <int SYS, bool BF16>
 static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
                                    bool pdl, cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
-  const size_t smem = staged_smem_bytes(P, tile.block, tile.chunk);  // + one producer warp
+  size_t smem = staged_smem_bytes(P, tile.block, tile.chunk);  // + one producer warp
   if (smem > (size_t)kStagedSmemMax) return cudaErrorInvalidValue;
+  // While the blocks fit on the SMs at once, each reserves kStagedSmemMax of
+  // shared memory (one block per SM).  Measured on GB300: with less (66 KB
+  // for control-channel jumps, which need no jump records) blocks of the
+  // concurrent noise pass shared the rollout's SMs, and the MPC step of the
+  // K = 4096 quadrotor with control-channel jumps took 0.427 ms against
+  // 0.280 ms with the reservation (0.344 ms with 100 KB).
+  if (blocks <= num_sms_of_current()) smem = (size_t)kStagedSmemMax;
   if (tile.chunk == 4)
     launch_hi(rollout_staged_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
