@@ -70,9 +70,8 @@ NCU_TRAFFIC = {
     ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105189888 + 3036928,
 }
 
-VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged", 4: "async"}
-ROLLOUT_KERNELS = {1: "rollout_kernel", 2: "rollout_split_kernel", 3: "rollout_staged_kernel",
-                   4: "rollout_async_kernel"}
+VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged"}
+ROLLOUT_KERNELS = {1: "rollout_kernel", 2: "rollout_split_kernel", 3: "rollout_staged_kernel"}
 
 
 def _peaks():
