@@ -95,14 +95,28 @@ def test_other_rollout_tiles_match_oracle(cuda, tile):
 
 def test_large_quadrotor_sampled_and_full_update(cuda):
     """K=65536, T=200, dt=0.005, Laplace marks at 5/s, bfloat16 noise: every
-    rollout's counts and noise, costs of rollouts 0..1023 and the full update
-    against the oracle over all K."""
+    rollout's counts, marks, noise and cost, and the full update, against the
+    oracle over all K."""
     prob = W.large_quadrotor()
     x0, U = W.initial_state(prob), W.initial_controls(prob)
     g = parity.gpu_iteration(prob, x0, U, 0)
     r = parity.oracle_iteration(prob, x0, U, 0)
     rep = parity.compare_iteration(prob, U, g, r)
     _record("quadrotor_K65536_T200_bf16_laplace", rep)
+
+
+def test_maximum_rollout_count(cuda):
+    """K = 2^24, the largest rollout count the library accepts (T = 2, a jump
+    rate high enough for many jumps): every rollout's counts, marks and noise,
+    all K costs and the full update against the oracle."""
+    prob = W.cartpole_k1000(K=1 << 24, T=2, nu=20.0, name="cartpole_K16777216_T2")
+    x0 = W.random_state(prob, np.random.default_rng(24), 0.2)
+    U = W.random_controls(prob, np.random.default_rng(25), 0.5)
+    g = parity.gpu_iteration(prob, x0, U, 5)
+    r = parity.oracle_iteration(prob, x0, U, 5)
+    rep = parity.compare_iteration(prob, U, g, r)
+    assert rep["jumps"] > 100000
+    _record("cartpole_K16777216_T2", rep)
 
 
 def test_all_costs_non_finite_leaves_controls(cuda):
