@@ -147,37 +147,52 @@ mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg) 
   return MPPI_OK;
 }
 
+// How the staged rollout applies the problem's state jumps (kJumpNone,
+// kJumpDefault or kJumpRows).
+static int jump_mode(const DevProblem& P) {
+  if (P.jump_channel != MPPI_JUMP_STATE) return kJumpNone;
+  return P.jump_default ? kJumpDefault : kJumpRows;
+}
+
 // Dynamic shared memory of the staged rollout: two stages of S steps of the
-// block's delta_eff rows, jump records, (q = 4) counts and the S control rows,
-// plus four mbarriers.
+// block's delta_eff rows, jump records (state jumps), counts (state jumps on
+// other rows) and the S control rows, plus four mbarriers.
 static size_t staged_smem_bytes(const DevProblem& P, int block, int S) {
   const size_t sb = P.noise_bf16 ? 2 : 4;
-  const bool sj = P.jump_channel == MPPI_JUMP_STATE;
-  const size_t per_step = (size_t)block * (P.m * sb + (sj ? 16 : 0) + (sj && P.q > 3 ? 1 : 0));
+  const int jm = jump_mode(P);
+  const size_t per_step = (size_t)block * (P.m * sb + (jm != kJumpNone ? 16 : 0) + (jm == kJumpRows ? 1 : 0));
   const size_t u_rows = ((size_t)S * P.m * 4 + 15) & ~(size_t)15;
   return 2 * ((size_t)S * per_step + u_rows) + 32;
 }
 
 constexpr int kStagedSmemMax = 160 * 1024;
 
-template <int SYS, bool BF16>
+template <int SYS, bool BF16, int JM>
 static cudaError_t allow_staged_smem() {
-  cudaError_t e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 4>,
+  cudaError_t e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 4, JM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 8>,
+    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 8, JM>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 16>,
+    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 16, JM>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
   return e;
 }
 
+template <int SYS, bool BF16>
+static cudaError_t allow_staged_smem_all() {
+  cudaError_t e = allow_staged_smem<SYS, BF16, kJumpNone>();
+  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpDefault>();
+  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpRows>();
+  return e;
+}
+
 cudaError_t prepare_kernels() {
-  cudaError_t e = allow_staged_smem<0, false>();
-  if (e == cudaSuccess) e = allow_staged_smem<0, true>();
-  if (e == cudaSuccess) e = allow_staged_smem<1, false>();
-  if (e == cudaSuccess) e = allow_staged_smem<1, true>();
+  cudaError_t e = allow_staged_smem_all<0, false>();
+  if (e == cudaSuccess) e = allow_staged_smem_all<0, true>();
+  if (e == cudaSuccess) e = allow_staged_smem_all<1, false>();
+  if (e == cudaSuccess) e = allow_staged_smem_all<1, true>();
   return e;
 }
 
@@ -302,6 +317,20 @@ static void launch_seq_t(const DevProblem& P, const IterBuffers& b, const Rollou
         P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
 }
 
+template <int SYS, bool BF16, int JM>
+static void launch_staged_s(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile, int blocks,
+                            size_t smem, bool pdl, cudaStream_t s) {
+  if (tile.chunk == 4)
+    launch_hi(rollout_staged_kernel<SYS, BF16, 4, JM>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
+        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
+  else if (tile.chunk == 16)
+    launch_hi(rollout_staged_kernel<SYS, BF16, 16, JM>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
+        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
+  else
+    launch_hi(rollout_staged_kernel<SYS, BF16, 8, JM>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
+        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
+}
+
 template <int SYS, bool BF16>
 static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
                                    bool pdl, cudaStream_t s) {
@@ -315,15 +344,10 @@ static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, co
   // K = 4096 quadrotor with control-channel jumps took 0.427 ms against
   // 0.280 ms with the reservation (0.344 ms with 100 KB).
   if (blocks <= num_sms_of_current()) smem = (size_t)kStagedSmemMax;
-  if (tile.chunk == 4)
-    launch_hi(rollout_staged_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
-        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
-  else if (tile.chunk == 16)
-    launch_hi(rollout_staged_kernel<SYS, BF16, 16>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
-        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
-  else
-    launch_hi(rollout_staged_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
-        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
+  const int jm = jump_mode(P);
+  if (jm == kJumpNone) launch_staged_s<SYS, BF16, kJumpNone>(P, b, tile, blocks, smem, pdl, s);
+  else if (jm == kJumpDefault) launch_staged_s<SYS, BF16, kJumpDefault>(P, b, tile, blocks, smem, pdl, s);
+  else launch_staged_s<SYS, BF16, kJumpRows>(P, b, tile, blocks, smem, pdl, s);
   return cudaSuccess;
 }
 

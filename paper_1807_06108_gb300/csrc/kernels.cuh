@@ -127,16 +127,15 @@ __device__ __forceinline__ void load_noise(const void* __restrict__ noise, size_
   }
 }
 
-// One step of cost and dynamics shared by both rollout forms: the
+// One step of cost and dynamics shared by the rollout forms: the
 // k-dependent part of the augmented running cost of Eq. 34-35 in control
 // units (the term lambda/2 u^T Sigma^-1 u is the same for every rollout and
 // cancels in the weights; it is summed once per iteration by
-// control_cost_sum), the Euler step of Algorithm 1 with the control-affine
-// drift of Eq. 4, then the state jump when the step has one.
+// control_cost_sum) and the Euler step of Algorithm 1 with the control-affine
+// drift of Eq. 4.  A state-channel jump of the step follows (state_jump).
 template <int SYS>
 __device__ __forceinline__ void cost_and_step(const DevProblem& P, float* x, const float* u,
-                                              const float* de, bool jumped, const float J[4],
-                                              float& s, float& sc) {
+                                              const float* de, float& s, float& sc) {
   using PL = Plant<SYS>;
   constexpr int n = PL::n, m = PL::m;
   float uSd = 0.0f, dSd = 0.0f;
@@ -154,24 +153,37 @@ __device__ __forceinline__ void cost_and_step(const DevProblem& P, float* x, con
   PL::xdot(P.pl, x, v, xd);
 #pragma unroll
   for (int i = 0; i < n; ++i) x[i] += xd[i] * P.dt;
-  if (jumped && P.jump_channel == 0) {
-    if (P.jump_default) {
-      // the plant's velocity rows: (xdot, thetadot) or (vx, vy, vz)
-      if constexpr (SYS == 0) {
-        x[1] += P.s_jump * J[0];
-        x[3] += P.s_jump * J[1];
-      } else {
-        x[3] += P.s_jump * J[0];
-        x[4] += P.s_jump * J[1];
-        x[5] += P.s_jump * J[2];
-      }
-    } else {
+}
+
+// The state-channel jump of a step (Eq. 2, Algorithm 1), after its Euler
+// step: x[H rows] += s_J J, s_J = sqrt(dt) or 1.  state_jump_default serves
+// the plant's velocity rows, (xdot, thetadot) or (vx, vy, vz), and is applied
+// on every step (J is zero for a step without a jump), so the step loop has
+// no branch; state_jump serves any rows and is called only for steps with a
+// jump.
+template <int SYS>
+__device__ __forceinline__ void state_jump_default(const DevProblem& P, float* x, const float J[4]) {
+  if constexpr (SYS == 0) {
+    x[1] += P.s_jump * J[0];
+    x[3] += P.s_jump * J[1];
+  } else {
+    x[3] += P.s_jump * J[0];
+    x[4] += P.s_jump * J[1];
+    x[5] += P.s_jump * J[2];
+  }
+}
+
+template <int SYS>
+__device__ __forceinline__ void state_jump(const DevProblem& P, float* x, const float J[4]) {
+  constexpr int n = Plant<SYS>::n;
+  if (P.jump_default) {
+    state_jump_default<SYS>(P, x, J);
+  } else {
 #pragma unroll
-      for (int r = 0; r < n; ++r)
+    for (int r = 0; r < n; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (c < P.q && P.jump_rows[c] == r) x[r] += P.s_jump * J[c];
-    }
+      for (int c = 0; c < 4; ++c)
+        if (c < P.q && P.jump_rows[c] == r) x[r] += P.s_jump * J[c];
   }
 }
 
@@ -269,7 +281,11 @@ __device__ __forceinline__ void fused_rollout_thread(
       float u[m];
 #pragma unroll
       for (int i = 0; i < m; ++i) u[i] = COHERENT ? __ldcg(U + j * m + i) : __ldg(U + j * m + i);
-      cost_and_step<SYS>(P, x, u, de, N > 0, J, s, sc);
+      cost_and_step<SYS>(P, x, u, de, s, sc);
+      if (P.jump_channel == 0) {
+        if (P.jump_default) state_jump_default<SYS>(P, x, J);  // J = 0 without a jump
+        else if (N > 0) state_jump<SYS>(P, x, J);
+      }
       store_noise<m, BF16>(noise, (size_t)j * P.Kpad + k, de, active);
       if (DBG && active) {
         const size_t rk = (size_t)j * P.K + k;
@@ -436,7 +452,11 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
       const float J[4] = {rj[jj].x, rj[jj].y, rj[jj].z, rj[jj].w};
       const bool jumped = sj && (q4 ? rc[jj] > 0 : rj[jj].w > 0.5f);
       if (j + kAhead < T) fetch(jj, j + kAhead, rd[jj], ru[jj], rj[jj], rc[jj]);
-      cost_and_step<SYS>(P, x, u, de, jumped, J, s, sc);
+      cost_and_step<SYS>(P, x, u, de, s, sc);
+      if (sj) {
+        if (P.jump_default) state_jump_default<SYS>(P, x, J);  // a zero record without a jump
+        else if (jumped) state_jump<SYS>(P, x, J);
+      }
     }
   }
   finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
@@ -525,11 +545,23 @@ constexpr int kStatusTimeout = 4;               // MPPI_ETIMEOUT
 // sit in an allocation padded to 16 bytes).  Each compute thread reads a
 // step's data from shared memory at the start of the step.  Launch with
 // nt + 32 threads; dynamic shared memory 2 * (S * nt * (m*s_b + 16 + 1) +
-// round16(S * m * 4)) bytes + 32 (the counts region only when q = 4).
+// round16(S * m * 4)) bytes + 32 (the jump-record and count regions only for
+// state-channel jumps).
 // ---------------------------------------------------------------------------
 constexpr int kStagedMaxThreads = kRolloutThreads + 32;
 
-template <int SYS, bool BF16, int S>
+// How a staged rollout applies state-channel jumps (a template argument, so
+// that the step loop carries only what the problem needs):
+//   kJumpNone    jumps act on the controls (folded into delta_eff): no jump
+//                records are read;
+//   kJumpDefault jumps hit the plant's velocity rows: every step adds
+//                s_J J from its record, which is zero for a step without a
+//                jump, so the step loop has no branch;
+//   kJumpRows    any other rows: the counts are copied too, and a step reads
+//                its record and applies it only when its count is positive.
+constexpr int kJumpNone = 0, kJumpDefault = 1, kJumpRows = 2;
+
+template <int SYS, bool BF16, int S, int JM>
 __global__ void __launch_bounds__(kStagedMaxThreads)
 rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
                       const void* __restrict__ noise, const uint8_t* __restrict__ counts,
@@ -541,11 +573,9 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
   const int nt = blockDim.x - 32, tid = threadIdx.x;  // compute threads, then the producer warp
   const int k0 = blockIdx.x * nt;
   const int nk = min(nt, P.Kpad - k0);
-  const bool sj = P.jump_channel == 0;
-  const bool q4 = P.q > 3;
   const int T = P.T;
-  const uint32_t d_stride = (uint32_t)nt * m * SB, j_stride = sj ? (uint32_t)nt * 16u : 0u,
-                 c_stride = (sj && q4) ? (uint32_t)nt : 0u;
+  const uint32_t d_stride = (uint32_t)nt * m * SB, j_stride = JM != kJumpNone ? (uint32_t)nt * 16u : 0u,
+                 c_stride = JM == kJumpRows ? (uint32_t)nt : 0u;
   const uint32_t u_off = S * (d_stride + j_stride + c_stride);  // control rows
   const uint32_t stage_bytes = u_off + ((S * m * 4 + 15) & ~15u);
   uint64_t* full = reinterpret_cast<uint64_t*>(stage_smem + 2 * stage_bytes);
@@ -567,8 +597,8 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
   if (tid >= nt) {
     // ---- producer warp: lane 0 issues every stage's copies
     if (tid != nt) return;
-    const uint32_t d_bytes = (uint32_t)nk * m * SB, j_bytes = sj ? (uint32_t)nk * 16u : 0u,
-                   c_bytes = (sj && q4) ? (uint32_t)nk : 0u;
+    const uint32_t d_bytes = (uint32_t)nk * m * SB, j_bytes = JM != kJumpNone ? (uint32_t)nk * 16u : 0u,
+                   c_bytes = JM == kJumpRows ? (uint32_t)nk : 0u;
     int issued = 0;
     bool ok = true, waited = false;
     for (int st = 0; st < n_stages && ok; ++st) {
@@ -627,7 +657,7 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
       const int j0 = st * S;
       const int ns = min(S, T - j0);
       // step data of step jj of this stage, from shared memory
-      auto fetch = [&](int jj, float* de, float* u, float4& jr, int& cnt) {
+      auto fetch = [&](int jj, float* de, float* u) {
         load_noise<m, BF16>(base + jj * d_stride, tid, de);
         if constexpr (m == 4) {
           const float4 u4 = reinterpret_cast<const float4*>(base + u_off)[jj];
@@ -638,12 +668,9 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
         } else {
           u[0] = reinterpret_cast<const float*>(base + u_off)[jj];
         }
-        jr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        cnt = 0;
-        if (sj) {
-          jr = reinterpret_cast<const float4*>(base + S * d_stride + jj * j_stride)[tid];
-          if (q4) cnt = base[S * (d_stride + j_stride) + jj * c_stride + tid];
-        }
+      };
+      auto record = [&](int jj) {
+        return reinterpret_cast<const float4*>(base + S * d_stride + jj * j_stride)[tid];
       };
       // Each step reads its data from shared memory at its start.  Long
       // stages (one block per SM, one warp per scheduler) unroll four steps,
@@ -656,12 +683,19 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
 #pragma unroll kUnroll
       for (int jj = 0; jj < ns; ++jj) {
         float de[m], u[m];
-        float4 jr;
-        int cnt;
-        fetch(jj, de, u, jr, cnt);
-        const float J[4] = {jr.x, jr.y, jr.z, jr.w};
-        const bool jumped = sj && (q4 ? cnt > 0 : jr.w > 0.5f);
-        cost_and_step<SYS>(P, x, u, de, jumped, J, s, sc);
+        fetch(jj, de, u);
+        cost_and_step<SYS>(P, x, u, de, s, sc);
+        if constexpr (JM == kJumpDefault) {
+          const float4 jr = record(jj);  // zero for a step without a jump
+          const float J[4] = {jr.x, jr.y, jr.z, jr.w};
+          state_jump_default<SYS>(P, x, J);
+        } else if constexpr (JM == kJumpRows) {
+          if (base[S * (d_stride + j_stride) + jj * c_stride + tid] > 0) {
+            const float4 jr = record(jj);
+            const float J[4] = {jr.x, jr.y, jr.z, jr.w};
+            state_jump<SYS>(P, x, J);
+          }
+        }
       }
     }
     // this warp is done with the buffer
