@@ -64,10 +64,10 @@ L2_BYTES = 129 * 1024 * 1024
 # profiles/quadrotor_K65536_T200_it5_bf16_kernels.md); None where no capture
 # of the current kernel exists.
 NCU_TRAFFIC = {
-    ("quadrotor_K4096_T100_it10", "rollout_staged_kernel"): 13149440 + 0,
+    ("quadrotor_K4096_T100_it10", "rollout_staged_kernel"): 13131264 + 0,
     ("quadrotor_K4096_T100_it10", "update_kernel"): 6630144 + 0,
-    ("quadrotor_K65536_T200_it5_bf16", "rollout_staged_kernel"): 314621440 + 3227136,
-    ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105189888 + 3036928,
+    ("quadrotor_K65536_T200_it5_bf16", "rollout_staged_kernel"): 314606080 + 3444224,
+    ("quadrotor_K65536_T200_it5_bf16", "update_kernel"): 105188864 + 2972928,
 }
 
 VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged"}
