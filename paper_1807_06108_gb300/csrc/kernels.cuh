@@ -529,8 +529,9 @@ constexpr int kStatusTimeout = 4;               // MPPI_ETIMEOUT
 // Split form, part 2, staged.  rollout_staged_kernel: the same per-rollout
 // sequential dynamics as rollout_split_kernel, but the step data of the
 // block's rollouts (delta_eff rows, and the jump records and counts as the
-// jump mode needs them) is moved into shared memory by the bulk-copy engine, S steps per stage, two stages in flight.
-// The block is nt compute threads (one per rollout) plus one producer warp.
+// jump mode needs them) is moved into shared memory by the bulk-copy engine,
+// S steps per stage, two stages in flight.  The block is nt compute threads
+// (one per rollout) plus one producer warp.
 // Each stage buffer has a "full" mbarrier (the copies landed) and an "empty"
 // one (every compute warp is done with it): a compute warp waits for "full",
 // runs its S steps from shared memory, releases the buffer and moves on; the
