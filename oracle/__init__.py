@@ -106,6 +106,10 @@ def _load():
             lib.orc_terminal_cost.restype = ctypes.c_double
             lib.orc_bf16_round.argtypes = [ctypes.c_double]
             lib.orc_bf16_round.restype = ctypes.c_double
+            lib.orc_bf16_ambiguous.argtypes = [ctypes.c_double]
+            lib.orc_bf16_ambiguous.restype = ctypes.c_int
+            lib.orc_obstacle_margin.argtypes = [pp, _d]
+            lib.orc_obstacle_margin.restype = ctypes.c_double
             lib.orc_rollouts.argtypes = [pp, _d, _d, ctypes.c_uint32, ctypes.c_int32,
                                          ctypes.c_int32, _d, _u8, _d, _d, _u8, _d, _d,
                                          ctypes.c_int32]
@@ -220,6 +224,14 @@ def bf16_round(x):
     return _load().orc_bf16_round(float(x))
 
 
+def bf16_ambiguous(x):
+    """True when the float64 value x lies within 2^-20 |x| of the midpoint
+    between the two bfloat16 neighbours of float32(x) (the rollouts whose
+    stored bfloat16 perturbation may legitimately differ between a float32
+    and a float64 computation)."""
+    return bool(_load().orc_bf16_ambiguous(float(x)))
+
+
 # --------------------------------------------------------------------------
 # Plants and costs
 # --------------------------------------------------------------------------
@@ -238,6 +250,13 @@ def state_cost(prob, x):
     P = make_problem(prob)
     x = _f64(x)
     return _load().orc_state_cost(ctypes.byref(P), _ptr(x, _d))
+
+
+def obstacle_margin(prob, x):
+    """|p - obs|^2 - obs_r^2 of the quadrotor state x (inf for the cart-pole)."""
+    P = make_problem(prob)
+    x = _f64(x)
+    return _load().orc_obstacle_margin(ctypes.byref(P), _ptr(x, _d))
 
 
 def terminal_cost(prob, x):

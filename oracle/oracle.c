@@ -341,6 +341,9 @@ static int bf16_ambiguous(double d) {
 
 double orc_bf16_round(double d) { return (double)bf16_round((float)d); }
 
+/* The ambiguity test above, exported for the tests that pin it. */
+int orc_bf16_ambiguous(double d) { return bf16_ambiguous(d); }
+
 /* ------------------------------------------------------------------------ */
 /* One rollout (the inner loop of Algorithm 1) for rollout index k.          */
 /*   delta_{j,i} = sqrt(c) sigma_i z          (eps ~ N(0, c Sigma_D))        */
