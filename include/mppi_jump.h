@@ -249,14 +249,14 @@ mppi_status mppi_jump_get_free_energy(mppi_jump_ctx* ctx, float out_host[3]);
 mppi_status mppi_jump_get_state(mppi_jump_ctx* ctx, void* buf_host, size_t* size_host);
 mppi_status mppi_jump_set_state(mppi_jump_ctx* ctx, const void* buf_host, size_t size);
 
-/* Allocation-free weights + weighted update, for callers that cannot
- * allocate device memory while they run: a fixed-rate control loop (a
- * cudaMalloc or cudaFree may synchronise the device and take unbounded time)
- * or a program whose device memory belongs to another allocator or a fixed
- * memory plan.  The paper has no counterpart; it computes what
- * mppi_jump_update computes (the weights of Eq. 36-37 and U += alpha * the
- * weighted mean of the perturbations, Eq. 37/49, without the MPC shift) from
- * caller-supplied arrays, all DEVICE pointers:
+/* Allocation-free weights + weighted update.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * while they run -- a fixed-rate control loop (a cudaMalloc or cudaFree may
+ * synchronise the device and take unbounded time) or a program whose device
+ * memory belongs to another allocator or a fixed memory plan.  It computes
+ * what mppi_jump_update computes (the softmin weights of the rollout costs
+ * and U += alpha * the weighted mean of the perturbations, without the MPC
+ * shift) from caller-supplied arrays, all DEVICE pointers:
  *   costs [K] rollout costs S~ (non-finite entries get weight 0),
  *   noise [T][K][m] float32 perturbations delta_eff, step-major,
  *   U [T][m] controls, updated in place.
@@ -267,10 +267,13 @@ mppi_status mppi_jump_set_state(mppi_jump_ctx* ctx, const void* buf_host, size_t
  * this library holds until the process exits.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress), so make the
  * first call on each device outside any stream capture.  Every call shares
- * the array: calls whose work overlaps on the GPU race and must be
- * serialised by the caller.  Returns MPPI_ENOMEM when
- * 64 + ceil(K/1024) * (T*m + 1) floats exceed the scratch, MPPI_EINVAL for
- * bad arguments; if every cost is non-finite, U is left unchanged. */
+ * the array and clears its control words first: calls whose work overlaps on
+ * the GPU race and must be serialised by the caller.  Limits: T <= 524280
+ * (8 steps per block along the grid's y dimension) and
+ * 64 + ceil(K/1024) * (T*m + 1) floats within the scratch.  Returns
+ * MPPI_EINVAL for bad arguments or T beyond its limit and MPPI_ENOMEM when
+ * the scratch is too small, in both cases before any work is enqueued; if
+ * every cost is non-finite, U is left unchanged. */
 mppi_status mppi_jump_update_noalloc(const float* costs, const float* noise, int32_t K, int32_t T,
                                      int32_t m, float lambda, float alpha, float* U, void* stream);
 

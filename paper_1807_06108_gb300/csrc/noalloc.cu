@@ -33,6 +33,7 @@ constexpr int kNaPerThread = 4;                     // rollouts per thread in a 
 constexpr int kNaChunk = kNaThreads * kNaPerThread;  // rollouts per block
 constexpr int kNaRows = 8;                          // steps per block
 constexpr int kMaxDevices = 64;
+constexpr int kMaxGroups = 65535;                   // gridDim.y limit
 
 static __device__ __align__(256) float g_update_scratch[kScratchFloats];
 
@@ -177,6 +178,9 @@ extern "C" mppi_status mppi_jump_update_noalloc(const float* costs, const float*
     return MPPI_EINVAL;
   const int chunks = (K + kNaChunk - 1) / kNaChunk;
   const int groups = (T + kNaRows - 1) / kNaRows;
+  // the step groups are the grid's y dimension, which holds at most 65535
+  // blocks: T <= 8 * 65535; checked before anything is enqueued
+  if (groups > kMaxGroups) return MPPI_EINVAL;
   const size_t need = (size_t)kCtlFloats + (size_t)chunks * T * m + (size_t)chunks;
   if (need > kScratchFloats) return MPPI_ENOMEM;  // beyond the fixed scratch
   float* scratch = nullptr;

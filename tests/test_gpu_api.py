@@ -42,7 +42,10 @@ def _one_iteration(prob, x0, U, it, tile):
     W.quadrotor_k4096(K=700, T=13, nu=9.0, jump_channel="control", noise_dtype="bf16",
                       mark_law="laplace"),
     W.quadrotor_k4096(K=300, T=21, nu=12.0, jump_rows=[3, 4, 5, 9], noise_dtype="bf16"),
-], ids=["cartpole", "quadrotor_state", "quadrotor_control_bf16", "quadrotor_q4_state_bf16"])
+    W.cartpole_k1000(K=500, T=19, nu=10.0, jump_rows=[0, 2], noise_dtype="bf16"),
+    W.quadrotor_k4096(K=400, T=23, nu=10.0, jump_rows=[0, 1, 2], mark_scale=0.2),
+], ids=["cartpole", "quadrotor_state", "quadrotor_control_bf16", "quadrotor_q4_state_bf16",
+        "cartpole_rows02_bf16", "quadrotor_rows012"])
 def test_rollout_tiles_are_bit_identical(cuda, prob):
     rng = np.random.default_rng(0)
     x0, U = W.random_state(prob, rng, 0.1), W.random_controls(prob, rng, 0.2)

@@ -113,3 +113,47 @@ def test_stalled_dependency_times_out_and_recovers(cuda):
         b.step(states)  # the batch is usable again
     finally:
         b.close()
+
+
+def test_full_batched_workload_matches_oracle_and_plain_path(cuda):
+    """All 256 instances of the batched workload (bfloat16 noise, K up to
+    8192, T up to 150, 35k work items on the persistent grid), two batched
+    steps: a fixed subset of 38 instances -- every instance with K = 8192 and
+    T >= 140 (both plants) and every eighth instance -- against the oracle's
+    MPC step, and every instance against the plain one-context path."""
+    from paper_1807_06108_gb300 import mppi
+    probs = W.batched_instances()
+    assert len(probs) == 256
+    big = [i for i, p in enumerate(probs) if p["K"] == 8192 and p["T"] >= 140]
+    assert {probs[i]["system"] for i in big} == {"cartpole", "quadrotor"}
+    subset = sorted(set(big) | set(range(0, 256, 8)))
+    assert len(subset) >= 32
+    rng = np.random.default_rng(3)
+    b = mppi.Batch(probs)
+    solvers = [mppi.Solver(p) for p in probs]
+    try:
+        U_in = [W.initial_controls(p) for p in probs]
+        for step in range(2):
+            states = _states(probs, rng)
+            u0s = b.step(states)
+            U_out = [b.controls(i) for i in range(len(probs))]
+            if step == 0:
+                sub = [probs[i] for i in subset]
+                _check_against_oracle(sub, [states[i] for i in subset], [U_in[i] for i in subset],
+                                      [0] * len(subset), [u0s[i] for i in subset],
+                                      [U_out[i] for i in subset])
+            for i, (p, s) in enumerate(zip(probs, solvers)):
+                s.set_controls(U_in[i])  # the same starting controls as the batch
+                u0_p = s.step(states[i])
+                U_p = s.controls()
+                U0 = np.asarray(U_in[i], dtype=np.float64)
+                den = max(np.max(np.abs(U_p[:-1] - U0[1:])), np.max(np.abs(u0_p - U0[0])), 1e-30)
+                err = max(np.max(np.abs(U_out[i] - U_p)), np.max(np.abs(u0s[i] - u0_p))) / den
+                assert err <= 1e-4 * p["iters"], (step, p["name"], err)
+            assert [b.iteration(i) for i in range(len(probs))] == \
+                [(step + 1) * p["iters"] for p in probs]
+            U_in = U_out
+    finally:
+        b.close()
+        for s in solvers:
+            s.close()

@@ -65,6 +65,17 @@ def _cases():
     p = W.quadrotor_k4096(K=515, T=27, nu=12.0, jump_rows=[3, 4, 5, 9], mark_scale=0.5)
     r = rng(7)
     c["quadrotor_q4_state_rows"] = (p, W.random_state(p, r, 0.1), W.random_controls(p, r, 0.2), 6)
+    # state jumps on rows other than the velocities with q <= 3 (the counted,
+    # per-step jump path), float32 and bfloat16 noise
+    for dt_ in ("f32", "bf16"):
+        p = W.cartpole_k1000(K=700, T=33, nu=10.0, jump_rows=[0, 2], noise_dtype=dt_)
+        r = rng(20)
+        c[f"cartpole_rows02_{dt_}"] = (p, W.random_state(p, r), W.random_controls(p, r), 7)
+        p = W.quadrotor_k4096(K=600, T=29, nu=10.0, jump_rows=[0, 1, 2], mark_scale=0.2,
+                              lam=20.0, noise_dtype=dt_)
+        r = rng(21)
+        c[f"quadrotor_rows012_{dt_}"] = (p, W.random_state(p, r, 0.1),
+                                         W.random_controls(p, r, 0.2), 8)
     p = W.quadrotor_alg1()
     r = rng(8)
     c["quadrotor_alg1_K4096_T100"] = (p, W.random_state(p, r, 0.1), W.random_controls(p, r, 0.2), 12)
@@ -91,6 +102,17 @@ def test_other_rollout_tiles_match_oracle(cuda, tile):
     prob, x0, U, it = CASES["quadrotor_laplace_bf16_sqrtdt"]
     rep = parity.run_and_compare(prob, x0, U, it, tile=tile)
     _record(f"quadrotor_laplace_bf16_sqrtdt_tile{tile}", rep)
+
+
+@pytest.mark.parametrize("tile", [(1, 64, 4), (2, 96, 8), (3, 32, 4), (3, 128, 16)],
+                         ids=["fused", "split", "staged_small_blocks", "staged_long_stages"])
+@pytest.mark.parametrize("name", ["cartpole_rows02_f32", "cartpole_rows02_bf16",
+                                  "quadrotor_rows012_f32", "quadrotor_rows012_bf16"])
+def test_non_default_jump_rows_every_tile_matches_oracle(cuda, name, tile):
+    prob, x0, U, it = CASES[name]
+    rep = parity.run_and_compare(prob, x0, U, it, tile=tile)
+    assert rep["jumps"] > 100
+    _record(f"{name}_tile{tile}", rep)
 
 
 def test_large_quadrotor_sampled_and_full_update(cuda):

@@ -115,3 +115,38 @@ def test_bad_requests_rejected(cuda):
             srv.submit(7, np.zeros(12))
     finally:
         srv.close()
+
+
+def test_served_workload_alone_equals_in_mix(cuda):
+    """The 64 sessions of the served workload (mixed plants, K up to 16384,
+    T up to 200, one or ten iterations per request) under the 20 GB budget:
+    three requests per session, all submitted at once and interleaved, so
+    that up to 32 run concurrently; every session's u0 sequence and final
+    controls equal, bit for bit, the same requests run alone through the
+    plain context path."""
+    from paper_1807_06108_gb300 import mppi
+    probs = W.served_sessions()
+    assert len(probs) == 64 and max(p["K"] for p in probs) == 16384
+    assert max(p["T"] for p in probs) == 200
+    xs = _trace(probs, 3, seed=4)
+    srv = mppi.Server(probs, budget_bytes=20 << 30, max_inflight=32)
+    try:
+        tickets = [[srv.submit(i, xs[i][k]) for i in range(len(probs))] for k in range(3)]
+        srv.drain(300)
+        mix = [[srv.wait(tickets[k][i]) for k in range(3)] for i in range(len(probs))]
+        U_mix = [srv.controls(i) for i in range(len(probs))]
+        st = srv.stats()
+        assert st["completed"] == 3 * len(probs) and st["evictions"] == 0
+    finally:
+        srv.close()
+    for i, p in enumerate(probs):
+        s = mppi.Solver(p)
+        try:
+            alone = [s.step(x) for x in xs[i]]
+            U_alone = s.controls()
+        finally:
+            s.close()
+        m = len(alone[0])
+        for a, b in zip(alone, mix[i]):
+            np.testing.assert_array_equal(a, b[:m])
+        np.testing.assert_array_equal(U_alone, U_mix[i])

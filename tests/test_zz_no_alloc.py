@@ -9,6 +9,7 @@ behind).  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1807_06108_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -45,6 +46,12 @@ def test_noalloc_update_matches_context_update(cuda, prob):
             dU = got - U_before
             err = np.max(np.abs(dU - dU_ref)) / max(np.max(np.abs(dU_ref)), 1e-30)
             assert err <= 1e-4, (call, err)
+            # and the FP64 oracle's weights and update from the same arrays
+            w, _ = oracle.softmin(S.astype(np.float64), prob["lam"])
+            U_or = oracle.update(w, noise.astype(np.float64), U_before, prob["alpha"])
+            dU_or = U_or - U_before
+            err_or = np.max(np.abs(dU - dU_or)) / max(np.max(np.abs(dU_or)), 1e-30)
+            assert err_or <= 1e-4, (call, err_or)
     finally:
         s.close()
 
@@ -60,4 +67,9 @@ def test_noalloc_rejects_sizes_beyond_the_scratch(cuda):
     assert e.value.code == mppi.ENOMEM
     with pytest.raises(mppi.MppiError) as e:
         mppi.mppi_jump_update_noalloc(p, p, 100, 10, 3, 1.0, 1.0, p)
+    assert e.value.code == mppi.EINVAL
+    # a horizon beyond 8 * 65535 steps is refused before anything is enqueued,
+    # even where its scratch would fit (one chunk of 1024 rollouts, m = 1)
+    with pytest.raises(mppi.MppiError) as e:
+        mppi.mppi_jump_update_noalloc(p, p, 1000, 8 * 65535 + 1, 1, 1.0, 1.0, p)
     assert e.value.code == mppi.EINVAL
