@@ -68,8 +68,9 @@ SEQ_OPS_PER_STEP = {"cartpole": 64.0, "quadrotor": 154.0}
 NOISE_OPS_PER_STEP = {"cartpole": 79.0, "quadrotor": 218.0}
 L2_BYTES = 129 * 1024 * 1024
 
-VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged"}
-ROLLOUT_KERNELS = {1: "rollout_kernel", 2: "rollout_split_kernel", 3: "rollout_staged_kernel"}
+VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged", 4: "staged_block_records"}
+ROLLOUT_KERNELS = {1: "rollout_kernel", 2: "rollout_split_kernel", 3: "rollout_staged_kernel",
+                   4: "rollout_staged_kernel"}
 
 # DRAM traffic per launch from ncu captures, with the hash of the kernel
 # sources they were taken on; a figure is reported only while the sources
@@ -361,6 +362,13 @@ def _config(prob, solves_per_s):
 # One single-problem workload
 # --------------------------------------------------------------------------
 
+def _launches_per_iteration(prob, tile):
+    if tile[0] == 1:
+        return 2
+    marks = prob["jump_channel"] == "state" and prob["nu"] > 0
+    return 4 if marks else 3
+
+
 def measure_workload(prob, args, steps, warmup, clk, dist, ws, local):
     """Times `steps` MPC solves of `prob` (after `warmup`), returns the
     record: value, ms_per_step, e2e, rooflines and launches."""
@@ -478,7 +486,13 @@ def measure_workload(prob, args, steps, warmup, clk, dist, ws, local):
     achieved = ops_step * K * T / (roll_avg / 1e3) / 1e12
     sb = 2 if prob["noise_dtype"] == "bf16" else 4
     m = 1 if prob["system"] == "cartpole" else 4
-    upd_bytes = K * T * m * sb + 8 * K + 8 * T * m
+    if tile[0] == 4:
+        # the update combines the rollout blocks' records (their perturbation
+        # pass runs inside the rollout kernel)
+        n_rec = (K + 31) // 32 * 32 // tile[1]
+        upd_bytes = n_rec * (2 + T * m) * 4 + 8 * T * m
+    else:
+        upd_bytes = K * T * m * sb + 8 * K + 8 * T * m
     upd_gbs = upd_bytes / (upd_iso_ms / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     rk = ROLLOUT_KERNELS[tile[0]]
@@ -490,9 +504,10 @@ def measure_workload(prob, args, steps, warmup, clk, dist, ws, local):
         "e2e": {"value": e2e, "unit": "trajectory-steps/s",
                 "h2d_bytes_per_step": 4 * len(x0), "d2h_bytes_per_step": 4 * m + 4,
                 "solves_per_s": e2e / steps_per_solve},
-        # per iteration: noise + rollout + update kernels (split and staged
-        # tiles) or rollout + update (fused tile), timed region A only
-        "gpu_launches": (2 if tile[0] == 1 else 3) * iters * steps,
+        # per iteration: noise (+ marks for state-channel jumps) + rollout +
+        # update (split and staged tiles) or rollout + update (fused tile),
+        # timed region A only
+        "gpu_launches": _launches_per_iteration(prob, tile) * iters * steps,
         "roofline": {"bound": "alu", "kernel": rk,
                      "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
                      "frac": achieved / alu_peak,
@@ -524,7 +539,7 @@ def bench_batched(reps=5):
     b = mppi.Batch(probs)
     try:
         b.set_states([W.initial_state(p) for p in probs])
-        block, _ = b.autotune(reps=2)
+        (block, chunk), _ = b.autotune(reps=2)
         info = b.info()
         b.step_async()
         b.sync()
@@ -564,7 +579,7 @@ def bench_batched(reps=5):
             "trajectory_steps_per_s": info["steps_per_solve"] / ms * 1e3,
             "one_instance_per_launch_ms": plain_ms,
             "one_instance_per_launch_solves_per_s": n / plain_ms * 1e3,
-            "speedup": plain_ms / ms, "block": block, "work_items": info["items"],
+            "speedup": plain_ms / ms, "block": block, "chunk": chunk, "work_items": info["items"],
             "grid": info["grid"]}
 
 
@@ -730,7 +745,8 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="time the rollout tile the library's autotuner picks")
     ap.add_argument("--tile", default="",
-                    help="rollout tile 'variant,block,chunk' (1 fused, 2 split, 3 staged)")
+                    help="rollout tile 'variant,block,chunk' (1 fused, 2 split, 3 staged, "
+                         "4 staged with block records)")
     ap.add_argument("--served-seconds", type=float, default=60.0,
                     help="length of the served leg's Poisson arrival trace at 2000 requests/s")
     ap.add_argument("--only", choices=["batched", "served"],

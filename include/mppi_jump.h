@@ -52,7 +52,8 @@ typedef enum {
   MPPI_ECUDA = 3,      /* a CUDA runtime call failed */
   MPPI_ETIMEOUT = 4,   /* a bounded device wait gave up */
   MPPI_ENONFINITE = 5, /* every rollout cost was non-finite: U left unchanged */
-  MPPI_EBUSY = 6       /* resource in use (e.g. session already has a request) */
+  MPPI_EBUSY = 6,      /* resource in use (e.g. session already has a request) */
+  MPPI_EBOUNDS = 7     /* a kernel's launch check failed (MPPI_CHECK_BOUNDS builds only) */
 } mppi_status;
 
 typedef enum { MPPI_CARTPOLE = 0, MPPI_QUADROTOR = 1 } mppi_system;
@@ -171,6 +172,36 @@ mppi_status mppi_jump_rollout_cost(mppi_jump_ctx* ctx, const float* x0, float* c
  * unchanged and the next synchronising call returns MPPI_ENONFINITE. */
 mppi_status mppi_jump_update(mppi_jump_ctx* ctx);
 
+/* Rollout sharding: one problem's rollouts split over several contexts
+ * (typically one per GPU).  Eq. 37 is a ratio of two sums over the rollouts,
+ * which are independent (Sec. V runs them in parallel), so a shard reduces its
+ * rollouts to a partial record and the records combine exactly, up to
+ * rounding.  A shard is a context whose configuration has K = the shard's
+ * rollout count and whose rollout offset is the index k0 of its first rollout
+ * in the unsharded problem: its rollouts draw the random numbers of rollouts
+ * k0 .. k0+K-1.
+ * mppi_jump_set_rollout_offset: sets k0 (default 0; k0 + K must stay below
+ *   2^32; drops the cached step graphs).
+ * mppi_jump_rollout_partial: rollout_cost from x0 [n] (device) for the current
+ *   counter, then writes the shard's partial record partial [2 + T*m]
+ *   (device): rho_g = min_k S~_k, Z_g = sum_k e_k and N_g[j][i] =
+ *   sum_k e_k delta_eff[j][k][i] with e_k = exp(-(S~_k - rho_g)/lambda)
+ *   (S~ without the rollout-independent control cost).  U and the counter are
+ *   unchanged.  A shard whose costs are all non-finite writes (+inf, 0, 0 ...).
+ * mppi_jump_apply_partials: combines n_parts records [n_parts][2 + T*m]
+ *   (device, 1 .. 4096 of them) with rho = min_g rho_g,
+ *   Z = sum_g Z_g exp(-(rho_g - rho)/lambda) and N likewise, applies
+ *   U += alpha_r N / Z (alpha_r = alpha * alpha_decay^r, iteration r of an MPC
+ *   step); shift != 0 also executes u0 [m] (device, may be NULL), shifts and
+ *   appends u_init; the counter advances by one.  Shards that apply the same
+ *   records in the same order keep bit-identical controls.  If every record
+ *   has rho = +inf, U is unchanged and the next synchronising call returns
+ *   MPPI_ENONFINITE. */
+mppi_status mppi_jump_set_rollout_offset(mppi_jump_ctx* ctx, uint32_t k_offset);
+mppi_status mppi_jump_rollout_partial(mppi_jump_ctx* ctx, const float* x0, float* partial);
+mppi_status mppi_jump_apply_partials(mppi_jump_ctx* ctx, const float* partials, int32_t n_parts,
+                                     int32_t r, int32_t shift, float* u0);
+
 /* A5 (Algorithm 1 MPC loop): `iters` x (rollout_cost + update) from the same
  * x0, iteration r with step size alpha * alpha_decay^r, then u0 = U_0,
  * U_i <- U_{i+1}, U_{T-1} <- u_init.  The work is replayed from a CUDA graph
@@ -187,15 +218,21 @@ mppi_status mppi_jump_step_async(mppi_jump_ctx* ctx, const float* x0, int32_t it
  * pass over K x T/4 threads stores delta_eff and the jump counts, then one
  * thread per rollout runs the sequential dynamics (more parallelism when K
  * alone does not fill the GPU); 3 = staged: the split form with the step
- * data of each block's rollouts moved into shared memory by bulk copies.
+ * data of each block's rollouts moved into shared memory by bulk copies;
+ * 4 = staged, and each rollout block also reduces its own rollouts to the
+ * partial record of mppi_jump_rollout_partial (re-reading its perturbation
+ * rows through shared memory), so that the update only combines the blocks'
+ * records.
  * rollout_block: threads per block of the rollout kernel (32, 64, 96 or
- * 128).  rollout_chunk: for the split form, steps per unrolled chunk, i.e.
- * how many steps ahead its loads run (2, 4 or 8); for the staged form, steps
- * per shared-memory stage (4, 8 or 16); ignored by the fused form.  The
- * staged form launches one extra (producer) warp per block.  The default is
+ * 128).  rollout_chunk: for the split form, how many steps ahead its loads
+ * run (2, 4 or 8); for the staged forms, steps per shared-memory stage (4, 8
+ * or 16); for the fused form, steps per unrolled chunk (4, 8 or 16).  The
+ * staged forms launch one extra (producer) warp per block.  The default is
  * staged, block 128, with 16-step stages while the rollout blocks fit on the
  * SMs about once and 8-step stages from two waves of blocks on.  Every tile
- * computes identical results.  Setting a tile drops the cached graphs. */
+ * computes identical costs; tiles 1-3 give identical updates, tile 4 the
+ * same update up to the summation order.  Setting a tile drops the cached
+ * graphs. */
 typedef struct {
   int32_t rollout_variant;
   int32_t rollout_block;
@@ -206,7 +243,8 @@ mppi_status mppi_jump_get_tuning(mppi_jump_ctx* ctx, mppi_jump_tuning* tuning_ho
 
 /* Autotuner: times the MPC step (graph replay, `iters` iterations from the
  * device state x0 [n]) for every rollout tile (fused x block 32, 64, 128;
- * split x block 32, 64, 128 x chunk 2, 4, 8), `reps` timed steps each after
+ * split x block 32, 64, 128 x chunk 2, 4, 8; staged and staged with block
+ * records x blocks and stages), `reps` timed steps each after
  * one warm-up, with CUDA events on the
  * context's stream, and keeps the fastest.  U and the iteration counter are
  * restored afterwards, so tuning does not change later results (every tile
@@ -226,7 +264,10 @@ mppi_status mppi_jump_enable_timing(mppi_jump_ctx* ctx, int32_t on);
 mppi_status mppi_jump_phase_times(mppi_jump_ctx* ctx, float out_host[2], int32_t* iters_host);
 
 /* Synchronises the context's stream and returns (then clears) the device
- * status word: MPPI_OK or MPPI_ENONFINITE. */
+ * status word: MPPI_OK, MPPI_ENONFINITE, MPPI_ETIMEOUT or (debug builds with
+ * MPPI_CHECK_BOUNDS, libmppi_jump_checked.so) MPPI_EBOUNDS: a kernel found
+ * its launch geometry or shared memory inconsistent with its problem and
+ * returned before touching memory; the context should then be destroyed. */
 mppi_status mppi_jump_sync(mppi_jump_ctx* ctx);
 
 /* Debug outputs of the following rollout_cost calls (NULL disables):
@@ -315,17 +356,24 @@ mppi_status mppi_batch_get_controls(mppi_batch* b, int32_t i, float* U);
 mppi_status mppi_batch_set_controls(mppi_batch* b, int32_t i, const float* U);
 mppi_status mppi_batch_get_iteration(mppi_batch* b, int32_t i, uint32_t* it_host);
 
-/* Tile: rollouts per block of the persistent kernel (64, 128 or 256). */
+/* Tile of the persistent kernel: block = rollouts per rollout item and
+ * threads per block (64, 128 or 256); chunk = steps per unrolled chunk of a
+ * rollout item (4 or 8: the chunk's random numbers are drawn together, so
+ * later steps' sampling overlaps earlier steps' dynamics).  Every tile
+ * computes the same costs.  set_tuning changes the block only. */
 mppi_status mppi_batch_set_tuning(mppi_batch* b, int32_t block);
 mppi_status mppi_batch_get_tuning(mppi_batch* b, int32_t* block_host);
+mppi_status mppi_batch_set_tile(mppi_batch* b, int32_t block, int32_t chunk);
+mppi_status mppi_batch_get_tile(mppi_batch* b, int32_t* block_host, int32_t* chunk_host);
 /* Failure-path test hook: with on != 0 the following steps start with a work
  * item whose dependency is never satisfied, so the step ends with
  * MPPI_ETIMEOUT after the bounded wait (about 2 s) instead of running; the
  * instances' controls may then be partially advanced.  on = 0 restores the
  * normal work list. */
 mppi_status mppi_batch_inject_stall(mppi_batch* b, int32_t on);
-/* Autotuner: times `reps` batched steps per block size from device x0s and
- * keeps the fastest; controls and counters are restored afterwards. */
+/* Autotuner: times `reps` batched steps for each tile (block 64, 128, 256 x
+ * chunk 4, 8) from device x0s and keeps the fastest (read it back with
+ * mppi_batch_get_tile); controls and counters are restored afterwards. */
 mppi_status mppi_batch_autotune(mppi_batch* b, const float* x0s, int32_t reps,
                                 int32_t* best_block_host, float* best_ms_host);
 /* Trajectory-steps of one batched step (sum of K_i T_i iters_i), the number of

@@ -2,8 +2,12 @@
 
 Each ``csrc/*.cu`` translation unit is compiled in parallel to an object file
 under ``_build/`` and linked into ``paper_1807_06108_gb300/_lib/libmppi_jump.so``
-(shared CUDA runtime).  Rebuilds only when a source or header is newer than
-the library.  No cmake, no torch extension machinery.
+(shared CUDA runtime).  ``checked=True`` builds the debug variant
+``libmppi_jump_checked.so`` (objects under ``_build_checked/``) with
+``-DMPPI_CHECK_BOUNDS``: every kernel checks its launch geometry and shared
+memory first and reports MPPI_EBOUNDS through the status word instead of
+touching memory.  Rebuilds only when a source or header is newer than the
+library.  No cmake, no torch extension machinery.
 """
 
 from __future__ import annotations
@@ -20,6 +24,7 @@ INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libmppi_jump.so")
+LIB_CHECKED = os.path.join(LIBDIR, "libmppi_jump_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
@@ -44,24 +49,28 @@ def _deps():
         os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    """Compile and link the library; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra_flags=(), checked=False):
+    """Compile and link the library (or its checked debug variant); returns
+    its path."""
+    lib = LIB_CHECKED if checked else LIB
+    objdir = BUILD + ("_checked" if checked else "")
+    flags = list(extra_flags) + (["-DMPPI_CHECK_BOUNDS"] if checked else [])
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     exe = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [exe, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [exe, *ARCH, *NVCC_FLAGS, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -72,16 +81,23 @@ def build(force=False, verbose=False, extra_flags=()):
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [exe, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force=False):
+    """The library and its checked variant, compiled side by side."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        futs = [ex.submit(build, force, False, (), c) for c in (False, True)]
+        return [f.result() for f in futs]
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build_all(force="--force" in sys.argv))

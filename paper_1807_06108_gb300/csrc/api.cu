@@ -1,6 +1,7 @@
 // api.cu -- the single-problem C ABI of libmppi_jump.so (see mppi_jump.h):
 // configuration, context lifetime, controls and counter, debug copies and
 // checkpointing.  The rollout / update / step calls are in step.cu.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -30,7 +31,8 @@ IterBuffers ctx_buffers(mppi_jump_ctx* ctx, float* costs, int set) {
   b.counts = ctx->counts[set];
   b.jrec = ctx->jrec[set];
   b.s_part = ctx->s_part;
-  b.w = ctx->w;
+  b.rec = ctx->rec;
+  b.max_chunks = ctx->max_chunks;
   b.partial = ctx->partial;
   b.zpart = ctx->zpart;
   b.gpart = ctx->gpart;
@@ -57,9 +59,13 @@ void drop_graphs(mppi_jump_ctx* ctx) {
 namespace {
 
 struct Layout {
-  size_t x0, U, noise[2], counts[2], jrec[2], s_part, w, partial, zpart, gpart, scal, status, it,
+  size_t x0, U, noise[2], counts[2], jrec[2], s_part, rec, partial, zpart, gpart, scal, status, it,
       rho_key, done, u0, total;
+  int max_chunks;
 };
+
+// Partial records the update may combine at once (rollout shards).
+constexpr int kMaxParts = 4096;
 
 Layout layout_of(const DevProblem& P, const UpdateGeom& g) {
   Layout L;
@@ -79,9 +85,16 @@ Layout layout_of(const DevProblem& P, const UpdateGeom& g) {
     L.jrec[s] = take(P.jump_channel == MPPI_JUMP_STATE ? sizeof(float4) * TK : 0);
   }
   L.s_part = take(sizeof(float) * P.Kpad);
-  L.w = take(sizeof(float) * P.Kpad);
-  L.partial = take(sizeof(float) * (size_t)g.chunks * P.T * P.m);
-  L.zpart = take(sizeof(float) * (size_t)g.groups * g.chunks);
+  // partial records of the rollout blocks (tile 4; the smallest block is 32)
+  const size_t max_blocks = ((size_t)P.Kpad + 31) / 32;
+  L.rec = take(sizeof(float) * max_blocks * (2 + (size_t)P.T * P.m));
+  // chunk partials of the update: rollout chunks, or chunks of records
+  const int bps = records_per_chunk(P.m);
+  L.max_chunks = g.chunks;
+  L.max_chunks = std::max(L.max_chunks, (int)((max_blocks + bps - 1) / bps));
+  L.max_chunks = std::max(L.max_chunks, (kMaxParts + bps - 1) / bps);
+  L.partial = take(sizeof(float) * (size_t)L.max_chunks * P.T * P.m);
+  L.zpart = take(sizeof(float) * (size_t)g.groups * L.max_chunks);
   L.gpart = take(sizeof(float) * (size_t)g.groups * (P.m + 1));
   L.scal = take(sizeof(float) * 8);
   L.status = take(sizeof(int) * 4);
@@ -111,6 +124,7 @@ const char* mppi_jump_status_string(mppi_status st) {
     case MPPI_ETIMEOUT: return "device wait timed out";
     case MPPI_ENONFINITE: return "all rollout costs non-finite";
     case MPPI_EBUSY: return "busy";
+    case MPPI_EBOUNDS: return "kernel launch check failed";
   }
   return "unknown status";
 }
@@ -242,10 +256,11 @@ mppi_status mppi_jump_init(const mppi_jump_config* cfg, void* stream, mppi_jump_
       for (int s = 0; s < 2; ++s) {
         ctx->noise[s] = a + L.noise[s];
         ctx->counts[s] = (uint8_t*)(a + L.counts[s]);
-        ctx->jrec[s] = (float4*)(a + L.jrec[s]);
+        ctx->jrec[s] = ctx->P.jump_channel == MPPI_JUMP_STATE ? (float4*)(a + L.jrec[s]) : nullptr;
       }
       ctx->s_part = (float*)(a + L.s_part);
-      ctx->w = (float*)(a + L.w);
+      ctx->rec = (float*)(a + L.rec);
+      ctx->max_chunks = L.max_chunks;
       ctx->partial = (float*)(a + L.partial);
       ctx->zpart = (float*)(a + L.zpart);
       ctx->gpart = (float*)(a + L.gpart);
@@ -353,7 +368,8 @@ mppi_status mppi_jump_get_noise(mppi_jump_ctx* ctx, void* noise) {
 
 mppi_status mppi_jump_get_weights(mppi_jump_ctx* ctx, float* weights) {
   if (!ctx || !weights) return MPPI_EINVAL;
-  CK(launch_normalize_weights(ctx->w, ctx->scal + 1, ctx->P.K, weights, ctx->stream), "get_weights");
+  CK(launch_weights(ctx->s_part, ctx->scal + 1, ctx->P.inv_lam, ctx->P.K, weights, ctx->stream),
+     "get_weights");
   return MPPI_OK;
 }
 

@@ -115,6 +115,11 @@ __device__ __forceinline__ UpdateArgs update_args(const BatchInst& I, int r) {
   UpdateArgs u;
   u.noise = I.noise;
   u.s_part = I.s_part;
+  u.rec = nullptr;  // the batched items stream the perturbations
+  u.nb = 0;
+  u.bps = 0;
+  u.rho_from_rec = 0;
+  u.export_out = nullptr;
   u.K = P.K;
   u.Kpad = P.Kpad;
   u.T = P.T;
@@ -149,17 +154,19 @@ __device__ __forceinline__ UpdateArgs update_args(const BatchInst& I, int r) {
   return u;
 }
 
-template <int NT, bool BF16, int SYS>
+template <int NT, bool BF16, int SYS, int CH>
 __device__ void run_rollout_item(const BatchInst& I, int r, int tile) {
   const DevProblem& P = I.P;
   const int k = tile * NT + threadIdx.x;
   // NT and Kpad are multiples of 32, so the k < Kpad test keeps whole warps
   if (k < P.Kpad)
-    fused_rollout_thread<SYS, BF16, false, true>(P, I.x0, I.U, __ldcg(I.it) + (uint32_t)r, k, I.s_part,
-                                                 I.noise, I.rho_key, nullptr, nullptr);
+    fused_rollout_thread<SYS, BF16, false, true, CH>(P, I.x0, I.U, __ldcg(I.it) + (uint32_t)r, k, I.s_part,
+                                                     I.noise, I.rho_key, nullptr, nullptr);
 }
 
-template <int NT, bool BF16>
+// NT: rollouts per rollout item (and threads per block); CH: steps per
+// unrolled chunk of a rollout item (4 or 8).
+template <int NT, bool BF16, int CH>
 __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
   // one shared scratch, viewed per channel count
   __shared__ __align__(16) unsigned char sh_raw[
@@ -199,8 +206,8 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
     const int r = (int)w.r;
     unsigned* signal;
     if (w.type == kItemR) {
-      if (I.P.system == 0) run_rollout_item<NT, BF16, 0>(I, r, (int)w.a);
-      else run_rollout_item<NT, BF16, 1>(I, r, (int)w.a);
+      if (I.P.system == 0) run_rollout_item<NT, BF16, 0, CH>(I, r, (int)w.a);
+      else run_rollout_item<NT, BF16, 1, CH>(I, r, (int)w.a);
       signal = I.done_R + r;
     } else {
       UpdateArgs u = update_args(I, r);
@@ -252,6 +259,7 @@ using namespace mj;
 struct mppi_batch {
   int n = 0;
   int block = 128;  // rollouts per block (persistent block size)
+  int chunk = 4;    // steps per unrolled chunk of a rollout item
   std::vector<mppi_jump_config> cfgs;
   std::vector<int> iters;
   std::vector<BatchInst> hinst;
@@ -288,7 +296,7 @@ mppi_status bfail(mppi_batch* b, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return bfail(b, e_, what);       \
   } while (0)
 
-template <int NT, bool BF16>
+template <int NT, bool BF16, int CH>
 cudaError_t launch_batch(mppi_batch* b, cudaStream_t s) {
   BatchArgs a;
   a.inst = b->d_inst;
@@ -298,31 +306,39 @@ cudaError_t launch_batch(mppi_batch* b, cudaStream_t s) {
   a.status = b->status;
   a.abort = b->status + 1;
   a.never = (const unsigned*)(b->status + 2);
-  batch_kernel<NT, BF16><<<b->grid, NT, 0, s>>>(a);
+  batch_kernel<NT, BF16, CH><<<b->grid, NT, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int NT, bool BF16>
+cudaError_t launch_batch_c(mppi_batch* b, cudaStream_t s) {
+  return b->chunk == 8 ? launch_batch<NT, BF16, 8>(b, s) : launch_batch<NT, BF16, 4>(b, s);
 }
 
 cudaError_t launch_batch_any(mppi_batch* b, cudaStream_t s) {
   const bool bf16 = b->cfgs[0].noise_dtype == MPPI_NOISE_BF16;
   switch (b->block) {
-    case 64: return bf16 ? launch_batch<64, true>(b, s) : launch_batch<64, false>(b, s);
-    case 256: return bf16 ? launch_batch<256, true>(b, s) : launch_batch<256, false>(b, s);
-    default: return bf16 ? launch_batch<128, true>(b, s) : launch_batch<128, false>(b, s);
+    case 64: return bf16 ? launch_batch_c<64, true>(b, s) : launch_batch_c<64, false>(b, s);
+    case 256: return bf16 ? launch_batch_c<256, true>(b, s) : launch_batch_c<256, false>(b, s);
+    default: return bf16 ? launch_batch_c<128, true>(b, s) : launch_batch_c<128, false>(b, s);
   }
 }
 
 template <int NT, bool BF16>
-int occupancy_of() {
+int occupancy_of(int chunk) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<NT, BF16>, NT, 0);
+  if (chunk == 8)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<NT, BF16, 8>, NT, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<NT, BF16, 4>, NT, 0);
   return per_sm;
 }
 
-int occupancy(int block, bool bf16) {
+int occupancy(int block, int chunk, bool bf16) {
   switch (block) {
-    case 64: return bf16 ? occupancy_of<64, true>() : occupancy_of<64, false>();
-    case 256: return bf16 ? occupancy_of<256, true>() : occupancy_of<256, false>();
-    default: return bf16 ? occupancy_of<128, true>() : occupancy_of<128, false>();
+    case 64: return bf16 ? occupancy_of<64, true>(chunk) : occupancy_of<64, false>(chunk);
+    case 256: return bf16 ? occupancy_of<256, true>(chunk) : occupancy_of<256, false>(chunk);
+    default: return bf16 ? occupancy_of<128, true>(chunk) : occupancy_of<128, false>(chunk);
   }
 }
 
@@ -384,7 +400,7 @@ mppi_status upload_plan(mppi_batch* b) {
   int sms = 152, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int occ = std::max(1, occupancy(b->block, b->cfgs[0].noise_dtype == MPPI_NOISE_BF16));
+  const int occ = std::max(1, occupancy(b->block, b->chunk, b->cfgs[0].noise_dtype == MPPI_NOISE_BF16));
   b->grid = sms * occ;
   BCK(cudaStreamSynchronize(b->stream), "plan upload");
   if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -393,6 +409,7 @@ mppi_status upload_plan(mppi_batch* b) {
 }
 
 mppi_status capture(mppi_batch* b) {
+  NvtxRange nv("mppi batch capture");
   if (b->graph) return MPPI_OK;
   cudaGraph_t g = nullptr;
   BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -560,10 +577,23 @@ mppi_status mppi_batch_info(mppi_batch* b, int64_t* steps_per_solve, int32_t* n_
 }
 
 mppi_status mppi_batch_set_tuning(mppi_batch* b, int32_t block) {
-  if (!b || (block != 64 && block != 128 && block != 256)) return MPPI_EINVAL;
-  BCK(cudaStreamSynchronize(b->stream), "set_tuning");
+  if (!b) return MPPI_EINVAL;
+  return mppi_batch_set_tile(b, block, b->chunk);
+}
+
+mppi_status mppi_batch_set_tile(mppi_batch* b, int32_t block, int32_t chunk) {
+  if (!b || (block != 64 && block != 128 && block != 256) || (chunk != 4 && chunk != 8)) return MPPI_EINVAL;
+  BCK(cudaStreamSynchronize(b->stream), "set_tile");
   b->block = block;
+  b->chunk = chunk;
   return upload_plan(b);
+}
+
+mppi_status mppi_batch_get_tile(mppi_batch* b, int32_t* block_host, int32_t* chunk_host) {
+  if (!b || !block_host || !chunk_host) return MPPI_EINVAL;
+  *block_host = b->block;
+  *chunk_host = b->chunk;
+  return MPPI_OK;
 }
 
 mppi_status mppi_batch_inject_stall(mppi_batch* b, int32_t on) {
@@ -580,6 +610,7 @@ mppi_status mppi_batch_get_tuning(mppi_batch* b, int32_t* block) {
 }
 
 mppi_status mppi_batch_step_async(mppi_batch* b, const float* x0s, float* u0s) {
+  NvtxRange nv("mppi batch step");
   if (!b || !x0s) return MPPI_EINVAL;
   mppi_status st = capture(b);
   if (st != MPPI_OK) return st;
@@ -666,12 +697,12 @@ mppi_status mppi_batch_autotune(mppi_batch* b, const float* x0s, int32_t reps, i
     cudaEventDestroy(e0);
     return bfail(b, cudaErrorUnknown, "events");
   }
-  const int cands[3] = {128, 64, 256};
-  int best = b->block;
+  const int cands[6][2] = {{128, 4}, {64, 4}, {256, 4}, {128, 8}, {64, 8}, {256, 8}};
+  int best = b->block, best_chunk = b->chunk;
   float best_t = 1e30f;
   mppi_status st = MPPI_OK;
-  for (int c : cands) {
-    st = mppi_batch_set_tuning(b, c);
+  for (const auto& c : cands) {
+    st = mppi_batch_set_tile(b, c[0], c[1]);
     if (st == MPPI_OK) st = mppi_batch_step_async(b, x0s, nullptr);
     if (st == MPPI_OK && cudaEventRecord(e0, b->stream) != cudaSuccess) st = MPPI_ECUDA;
     for (int r = 0; r < reps && st == MPPI_OK; ++r) st = mppi_batch_step_async(b, x0s, nullptr);
@@ -685,13 +716,14 @@ mppi_status mppi_batch_autotune(mppi_batch* b, const float* x0s, int32_t reps, i
     ms /= (float)reps;
     if (ms < best_t) {
       best_t = ms;
-      best = c;
+      best = c[0];
+      best_chunk = c[1];
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != MPPI_OK) return st;
-  st = mppi_batch_set_tuning(b, best);
+  st = mppi_batch_set_tile(b, best, best_chunk);
   for (int i = 0; i < b->n && st == MPPI_OK; ++i) {
     st = mppi_batch_set_controls(b, i, Us[i].data());
     if (st == MPPI_OK) {

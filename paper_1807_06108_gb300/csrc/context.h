@@ -24,13 +24,14 @@ struct mppi_jump_ctx {
   float* U = nullptr;           // [T][m]
   void* noise[2] = {};          // two sets of [T][Kpad][m] delta_eff (f32 or bf16)
   uint8_t* counts[2] = {};      // [T][Kpad] jump counts
-  float4* jrec[2] = {};         // [T][Kpad] state-jump step records
+  float4* jrec[2] = {};         // [T][Kpad] jump records (state jumps)
   float* s_part = nullptr;      // [Kpad]
-  float* w = nullptr;           // [Kpad] unnormalised weights
-  float* partial = nullptr;     // [chunks][T][m]
-  float* zpart = nullptr;       // [groups][chunks]
+  float* rec = nullptr;         // [ceil(Kpad/32)][2 + T*m] partial records of the rollout blocks
+  float* partial = nullptr;     // [max_chunks][T][m]
+  int max_chunks = 0;
+  float* zpart = nullptr;       // [groups][max_chunks]
   float* gpart = nullptr;       // [groups][m] edge values, [groups] control costs
-  float* scal = nullptr;        // cconst, diag[3]
+  float* scal = nullptr;        // cconst, diag[4] (rho~, Z, F, rho)
   int* status = nullptr;        // device status word
   uint32_t* it = nullptr;       // iteration counter
   uint32_t* rho_key = nullptr;  // running cost minimum

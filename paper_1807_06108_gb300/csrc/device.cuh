@@ -29,6 +29,7 @@ struct DevProblem {
   int32_t jump_default;  // state jumps hit the plant's velocity rows (1, 3) / (3, 4, 5)
   int32_t jump_rows[4];
   uint32_t key0, key1;
+  uint32_t k_base;  // Philox index of local rollout 0 (a rollout shard starts at k_base)
   uint32_t thr[kMaxJumps];  // jump-count thresholds (see the header)
   float dt, lam, inv_lam, is_coef, alpha, s_jump;
   float alpha_decay;  // step size alpha * alpha_decay^r at iteration r of a step
@@ -101,7 +102,7 @@ __device__ __forceinline__ int jump_count(const DevProblem& P, uint32_t w) {
 // u - 1/2 and 1 - 2|u - 1/2| are exact for the 23-bit uniforms above.
 __device__ __forceinline__ float laplace_mark(float b, uint32_t w) {
   const float h = uniform01(w) - 0.5f;
-  const float mag = -b * logf(1.0f - 2.0f * fabsf(h));
+  const float mag = __fmul_rn(-b, logf(1.0f - 2.0f * fabsf(h)));  // never fused with a later add
   return h > 0.0f ? mag : -mag;
 }
 

@@ -11,7 +11,24 @@
 #include "../../include/mppi_jump.h"
 #include "device.cuh"
 
+#ifndef MPPI_NO_NVTX
+#include <nvtx3/nvToolsExt.h>
+#endif
+
 namespace mj {
+
+// NVTX range around a host call (shown by profilers on the CPU timeline; a
+// no-op unless a profiler is attached; compiled out with MPPI_NO_NVTX).
+struct NvtxRange {
+#ifndef MPPI_NO_NVTX
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+#else
+  explicit NvtxRange(const char*) {}
+#endif
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Set a message into buf (size >= 256) and return st.
 mppi_status fail(char* buf, mppi_status st, const char* fmt, ...);
@@ -42,7 +59,9 @@ UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms);
 cudaError_t prepare_kernels();
 
 // Rollout launch shape: variant 1 = fused (one kernel draws and rolls out),
-// 2 = split (noise_kernel over K*T/4 threads, then rollout_split_kernel);
+// 2 = split (noise_kernel over K*T/4 threads, then rollout_split_kernel),
+// 3 = staged (the split form with bulk copies into shared memory), 4 =
+// staged, each block also forming its partial record for the update;
 // block = threads per block of the rollout kernel; chunk = steps per unrolled
 // chunk of the split rollout (its load-ahead depth: 2, 4 or 8).
 struct RolloutTile {
@@ -59,10 +78,11 @@ struct IterBuffers {
   float* U;
   void* noise;         // [T][Kpad][m] delta_eff, float32 or bfloat16
   uint8_t* counts;     // [T][Kpad] jump counts
-  float4* jrec;        // [T][Kpad] state-jump step records (split variant)
+  float4* jrec;        // [T][Kpad] jump records J (state jumps; zero without a jump)
   float* s_part;       // [Kpad] k-dependent cost part
-  float* w;            // [Kpad] unnormalised weights e_k
-  float* partial;      // [chunks][T][m]
+  float* partial;      // [chunks][T][m] (max_chunks chunks)
+  int max_chunks;      // chunks the partial and zpart buffers hold
+  float* rec;          // [ceil(Kpad/32)][2 + T*m] partial records of the rollout blocks
   float* zpart;        // [groups][chunks]
   float* gpart;        // [groups][m] shifted edge values, then [groups] control costs
   uint32_t* rho_key;   // running minimum of the costs (order key)
@@ -79,27 +99,44 @@ struct IterBuffers {
 
 // Split variant, part 1: noise of iteration *it + it_off into b.noise etc.
 cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s);
-// Split variant, part 2: the sequential rollout over the stored noise.  pdl:
-// launch as a programmatic dependent of the previous kernel in the stream,
-// which must then not be the noise pass that wrote b.noise (the staged
-// rollout starts copying step data before it waits for that kernel).
+// Split variant, part 2: the sequential rollout of iteration *it + it_off
+// over the stored noise.  pdl: launch as a programmatic dependent of the
+// previous kernel in the stream, which must then not be the noise pass that
+// wrote b.noise (the staged rollout starts copying step data before it waits
+// for that kernel).
 cudaError_t launch_rollout_seq(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
-                               bool pdl, cudaStream_t s);
+                               uint32_t it_off, bool pdl, cudaStream_t s);
 // Whole rollout (either variant) of iteration *it + it_off.  arm_min resets
 // the running cost minimum first (the update re-arms it after every
 // iteration, so only a rollout that follows no update needs it).
 cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
                            uint32_t it_off, bool arm_min, cudaStream_t s);
+// Where the update's partial sums come from: NULL, or rec == NULL, streams
+// the stored perturbations; otherwise nb partial records (rho_b, Z_b, N_b)
+// (of the rollout blocks of a tile-4 rollout, or of rollout shards) are
+// rescaled and summed, rho taken from the records (rho_from_rec) or from the
+// running minimum.  export_out != NULL writes the combined record
+// (rho, Z, N[T][m]) there instead of updating U.
+struct UpdateSource {
+  const float* rec;
+  int nb;
+  int rho_from_rec;
+  float* export_out;
+};
+// Records a chunk of the record-source update sums (m = 1 or 4).
+int records_per_chunk(int m);
 // Weights + update of iteration r of an MPC step (step size alpha *
 // alpha_decay^r); shift != 0 performs the MPC shift and writes u0 (if not
 // NULL); the counter advances by it_advance.  An ordinary launch (it
 // starts once the preceding kernel has completed).
 cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g, int r,
-                          int shift, uint32_t it_advance, float* u0, cudaStream_t s);
+                          int shift, uint32_t it_advance, float* u0, cudaStream_t s,
+                          const UpdateSource* src = nullptr);
 // costs[k] = S~_k (the full augmented cost) when b.costs is not NULL.
 cudaError_t launch_costs(const DevProblem& P, const IterBuffers& b, cudaStream_t s);
-// w_k = e_k / Z (Z = diag[1]) for the weights getter.
-cudaError_t launch_normalize_weights(const float* e, const float* diag, int K, float* w,
-                                     cudaStream_t s);
+// w_k = exp((rho - S~_k)/lambda) / Z (rho = diag[3], Z = diag[1]) for the
+// weights getter.
+cudaError_t launch_weights(const float* s_part, const float* diag, float inv_lam, int K, float* w,
+                           cudaStream_t s);
 
 }  // namespace mj

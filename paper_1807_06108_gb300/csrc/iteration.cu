@@ -155,36 +155,35 @@ static int jump_mode(const DevProblem& P) {
 }
 
 // Dynamic shared memory of the staged rollout: two stages of S steps of the
-// block's delta_eff rows, jump records (state jumps), counts (state jumps on
-// other rows) and the S control rows, plus four mbarriers.
-static size_t staged_smem_bytes(const DevProblem& P, int block, int S) {
-  const size_t sb = P.noise_bf16 ? 2 : 4;
-  const int jm = jump_mode(P);
-  const size_t per_step = (size_t)block * (P.m * sb + (jm != kJumpNone ? 16 : 0) + (jm == kJumpRows ? 1 : 0));
-  const size_t u_rows = ((size_t)S * P.m * 4 + 15) & ~(size_t)15;
-  return 2 * ((size_t)S * per_step + u_rows) + 32;
+// block's delta_eff rows, jump-mark table and counts (state jumps) and the S
+// control rows, the six mbarriers and the producer's jump list.
+static size_t staged_smem_bytes(const DevProblem& P, int block, int S, bool part) {
+  return staged_smem_total(block, P.m, P.noise_bf16 ? 2 : 4, S, jump_mode(P) != kJumpNone, part);
 }
 
 constexpr int kStagedSmemMax = 160 * 1024;
 
-template <int SYS, bool BF16, int JM>
+template <int SYS, bool BF16, int JM, bool PART>
 static cudaError_t allow_staged_smem() {
-  cudaError_t e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 4, JM>,
+  cudaError_t e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 4, JM, PART>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 8, JM>,
+    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 8, JM, PART>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 16, JM>,
+    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 16, JM, PART>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
   return e;
 }
 
 template <int SYS, bool BF16>
 static cudaError_t allow_staged_smem_all() {
-  cudaError_t e = allow_staged_smem<SYS, BF16, kJumpNone>();
-  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpDefault>();
-  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpRows>();
+  cudaError_t e = allow_staged_smem<SYS, BF16, kJumpNone, false>();
+  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpDefault, false>();
+  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpRows, false>();
+  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpNone, true>();
+  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpDefault, true>();
+  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpRows, true>();
   return e;
 }
 
@@ -274,68 +273,94 @@ RolloutTile default_tile(const DevProblem& P, int num_sms) {
 
 bool valid_tile(const RolloutTile& t) {
   if (t.block < 32 || t.block > kRolloutThreads || t.block % 32 != 0) return false;
-  if (t.variant == 3) return t.chunk == 4 || t.chunk == 8 || t.chunk == 16;
-  return (t.variant == 1 || t.variant == 2) && (t.chunk == 2 || t.chunk == 4 || t.chunk == 8);
+  // fused and staged forms: steps per unrolled chunk or per stage; split
+  // form: how many steps ahead its loads run
+  if (t.variant == 1 || t.variant == 3 || t.variant == 4) return t.chunk == 4 || t.chunk == 8 || t.chunk == 16;
+  return t.variant == 2 && (t.chunk == 2 || t.chunk == 4 || t.chunk == 8);
 }
 
-template <int M, bool BF16, bool DBG>
+template <int M, bool BF16, bool DBG, bool MARKS>
 static void launch_noise_t(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s) {
-  const long long nthreads = (long long)P.Kpad * ((P.T + 3) / 4);
-  const int nblocks = (int)((nthreads + kNoiseThreads - 1) / kNoiseThreads);
-  noise_kernel<M, BF16, DBG><<<nblocks, kNoiseThreads, 0, s>>>(
-      P, b.it, it_off, b.noise, b.counts, b.jrec, b.dbg_counts, b.dbg_J);
+  const dim3 grid((P.Kpad + kNoiseThreads - 1) / kNoiseThreads, (P.T + 3) / 4);
+  float4* jrec = P.jump_channel == MPPI_JUMP_STATE ? b.jrec : nullptr;
+  noise_kernel<M, BF16, DBG, MARKS><<<grid, kNoiseThreads, 0, s>>>(P, b.it, it_off, b.noise, b.counts, jrec,
+                                                                   b.dbg_counts, b.dbg_J, b.status);
+}
+
+template <int M, bool BF16>
+static void launch_noise_m(const DevProblem& P, const IterBuffers& b, uint32_t it_off, bool dbg,
+                           cudaStream_t s) {
+  // the marks are drawn here for control-channel jumps (folded into
+  // delta_eff) and for the debug copy of J; state-channel jumps are drawn by
+  // the rollout
+  if (dbg) launch_noise_t<M, BF16, true, true>(P, b, it_off, s);
+  else if (P.jump_channel == MPPI_JUMP_CONTROL) launch_noise_t<M, BF16, false, true>(P, b, it_off, s);
+  else launch_noise_t<M, BF16, false, false>(P, b, it_off, s);
 }
 
 cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s) {
   const bool dbg = b.dbg_counts != nullptr || b.dbg_J != nullptr;
-  const int sel = (P.m == 4 ? 4 : 0) + (P.noise_bf16 ? 2 : 0) + (dbg ? 1 : 0);
-  switch (sel) {
-    case 0: launch_noise_t<1, false, false>(P, b, it_off, s); break;
-    case 1: launch_noise_t<1, false, true>(P, b, it_off, s); break;
-    case 2: launch_noise_t<1, true, false>(P, b, it_off, s); break;
-    case 3: launch_noise_t<1, true, true>(P, b, it_off, s); break;
-    case 4: launch_noise_t<4, false, false>(P, b, it_off, s); break;
-    case 5: launch_noise_t<4, false, true>(P, b, it_off, s); break;
-    case 6: launch_noise_t<4, true, false>(P, b, it_off, s); break;
-    default: launch_noise_t<4, true, true>(P, b, it_off, s); break;
+  switch ((P.m == 4 ? 2 : 0) + (P.noise_bf16 ? 1 : 0)) {
+    case 0: launch_noise_m<1, false>(P, b, it_off, dbg, s); break;
+    case 1: launch_noise_m<1, true>(P, b, it_off, dbg, s); break;
+    case 2: launch_noise_m<4, false>(P, b, it_off, dbg, s); break;
+    default: launch_noise_m<4, true>(P, b, it_off, dbg, s); break;
+  }
+  // state-channel jumps: their marks into the jump records
+  if (P.jump_channel == MPPI_JUMP_STATE && P.nmax > 0) {
+    const int per_block = kMarkSpan * (kMarkThreads / 32);
+    const dim3 grid((P.Kpad + per_block - 1) / per_block, P.T);
+    marks_kernel<<<grid, kMarkThreads, 0, s>>>(P, b.it, it_off, b.counts, b.jrec, b.status);
   }
   return cudaGetLastError();
 }
 
 template <int SYS, bool BF16>
 static void launch_seq_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
-                         bool pdl, cudaStream_t s) {
+                         uint32_t it_off, bool pdl, cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
   if (tile.chunk == 2)
     launch_hi(rollout_split_kernel<SYS, BF16, 2>, dim3(blocks), dim3(tile.block), 0, s, pdl,
-        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
+        P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status);
   else if (tile.chunk == 8)
     launch_hi(rollout_split_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block), 0, s, pdl,
-        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
+        P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status);
   else
     launch_hi(rollout_split_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block), 0, s, pdl,
-        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key);
+        P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status);
 }
 
-template <int SYS, bool BF16, int JM>
+template <int SYS, bool BF16, int JM, bool PART>
 static void launch_staged_s(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile, int blocks,
-                            size_t smem, bool pdl, cudaStream_t s) {
+                            size_t smem, uint32_t it_off, bool pdl, cudaStream_t s) {
   if (tile.chunk == 4)
-    launch_hi(rollout_staged_kernel<SYS, BF16, 4, JM>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
-        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
+    launch_hi(rollout_staged_kernel<SYS, BF16, 4, JM, PART>, dim3(blocks), dim3(tile.block + 32), smem, s,
+        pdl, P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status, b.rec);
   else if (tile.chunk == 16)
-    launch_hi(rollout_staged_kernel<SYS, BF16, 16, JM>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
-        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
+    launch_hi(rollout_staged_kernel<SYS, BF16, 16, JM, PART>, dim3(blocks), dim3(tile.block + 32), smem, s,
+        pdl, P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status, b.rec);
   else
-    launch_hi(rollout_staged_kernel<SYS, BF16, 8, JM>, dim3(blocks), dim3(tile.block + 32), smem, s, pdl,
-        P, b.x0, b.U, b.noise, b.counts, b.jrec, b.s_part, b.rho_key, b.status);
+    launch_hi(rollout_staged_kernel<SYS, BF16, 8, JM, PART>, dim3(blocks), dim3(tile.block + 32), smem, s,
+        pdl, P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status, b.rec);
+}
+
+template <int SYS, bool BF16, bool PART>
+static void launch_staged_j(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile, int blocks,
+                            size_t smem, uint32_t it_off, bool pdl, cudaStream_t s) {
+  const int jm = jump_mode(P);
+  if (jm == kJumpNone) launch_staged_s<SYS, BF16, kJumpNone, PART>(P, b, tile, blocks, smem, it_off, pdl, s);
+  else if (jm == kJumpDefault)
+    launch_staged_s<SYS, BF16, kJumpDefault, PART>(P, b, tile, blocks, smem, it_off, pdl, s);
+  else launch_staged_s<SYS, BF16, kJumpRows, PART>(P, b, tile, blocks, smem, it_off, pdl, s);
 }
 
 template <int SYS, bool BF16>
 static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
-                                   bool pdl, cudaStream_t s) {
+                                   uint32_t it_off, bool pdl, cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
-  size_t smem = staged_smem_bytes(P, tile.block, tile.chunk);  // + one producer warp
+  const bool part = tile.variant == 4;
+  if (part && !b.rec) return cudaErrorInvalidValue;
+  size_t smem = staged_smem_bytes(P, tile.block, tile.chunk, part);
   if (smem > (size_t)kStagedSmemMax) return cudaErrorInvalidValue;
   // While the blocks fit on the SMs at once, each reserves kStagedSmemMax of
   // shared memory (one block per SM).  Measured on GB300: with less (66 KB
@@ -344,32 +369,30 @@ static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, co
   // K = 4096 quadrotor with control-channel jumps took 0.427 ms against
   // 0.280 ms with the reservation (0.344 ms with 100 KB).
   if (blocks <= num_sms_of_current()) smem = (size_t)kStagedSmemMax;
-  const int jm = jump_mode(P);
-  if (jm == kJumpNone) launch_staged_s<SYS, BF16, kJumpNone>(P, b, tile, blocks, smem, pdl, s);
-  else if (jm == kJumpDefault) launch_staged_s<SYS, BF16, kJumpDefault>(P, b, tile, blocks, smem, pdl, s);
-  else launch_staged_s<SYS, BF16, kJumpRows>(P, b, tile, blocks, smem, pdl, s);
+  if (part) launch_staged_j<SYS, BF16, true>(P, b, tile, blocks, smem, it_off, pdl, s);
+  else launch_staged_j<SYS, BF16, false>(P, b, tile, blocks, smem, it_off, pdl, s);
   return cudaSuccess;
 }
 
 cudaError_t launch_rollout_seq(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
-                               bool pdl, cudaStream_t s) {
+                               uint32_t it_off, bool pdl, cudaStream_t s) {
   if (!valid_tile(tile) || tile.variant == 1) return cudaErrorInvalidValue;
-  if (tile.variant == 3) {
+  if (tile.variant >= 3) {
     cudaError_t e = cudaSuccess;
     switch (P.system * 2 + (P.noise_bf16 ? 1 : 0)) {
-      case 0: e = launch_staged_t<0, false>(P, b, tile, pdl, s); break;
-      case 1: e = launch_staged_t<0, true>(P, b, tile, pdl, s); break;
-      case 2: e = launch_staged_t<1, false>(P, b, tile, pdl, s); break;
-      default: e = launch_staged_t<1, true>(P, b, tile, pdl, s); break;
+      case 0: e = launch_staged_t<0, false>(P, b, tile, it_off, pdl, s); break;
+      case 1: e = launch_staged_t<0, true>(P, b, tile, it_off, pdl, s); break;
+      case 2: e = launch_staged_t<1, false>(P, b, tile, it_off, pdl, s); break;
+      default: e = launch_staged_t<1, true>(P, b, tile, it_off, pdl, s); break;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
   switch (P.system * 2 + (P.noise_bf16 ? 1 : 0)) {
-    case 0: launch_seq_t<0, false>(P, b, tile, pdl, s); break;
-    case 1: launch_seq_t<0, true>(P, b, tile, pdl, s); break;
-    case 2: launch_seq_t<1, false>(P, b, tile, pdl, s); break;
-    default: launch_seq_t<1, true>(P, b, tile, pdl, s); break;
+    case 0: launch_seq_t<0, false>(P, b, tile, it_off, pdl, s); break;
+    case 1: launch_seq_t<0, true>(P, b, tile, it_off, pdl, s); break;
+    case 2: launch_seq_t<1, false>(P, b, tile, it_off, pdl, s); break;
+    default: launch_seq_t<1, true>(P, b, tile, it_off, pdl, s); break;
   }
   return cudaGetLastError();
 }
@@ -378,8 +401,15 @@ template <int SYS, bool BF16, bool DBG>
 static void launch_fused_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
                            uint32_t it_off, cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
-  launch_hi(rollout_kernel<SYS, BF16, DBG>, dim3(blocks), dim3(tile.block), 0, s, true, P, b.x0, b.U, b.it,
-            it_off, b.s_part, b.noise, b.rho_key, b.dbg_counts, b.dbg_J);
+  if (tile.chunk == 16)
+    launch_hi(rollout_kernel<SYS, BF16, DBG, 16>, dim3(blocks), dim3(tile.block), 0, s, true, P, b.x0, b.U,
+              b.it, it_off, b.s_part, b.noise, b.rho_key, b.dbg_counts, b.dbg_J, b.status);
+  else if (tile.chunk == 8)
+    launch_hi(rollout_kernel<SYS, BF16, DBG, 8>, dim3(blocks), dim3(tile.block), 0, s, true, P, b.x0, b.U,
+              b.it, it_off, b.s_part, b.noise, b.rho_key, b.dbg_counts, b.dbg_J, b.status);
+  else
+    launch_hi(rollout_kernel<SYS, BF16, DBG, 4>, dim3(blocks), dim3(tile.block), 0, s, true, P, b.x0, b.U,
+              b.it, it_off, b.s_part, b.noise, b.rho_key, b.dbg_counts, b.dbg_J, b.status);
 }
 
 cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
@@ -393,7 +423,7 @@ cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const Roll
     cudaError_t e = launch_noise(P, b, it_off, s);
     if (e != cudaSuccess) return e;
     // the rollout reads what the noise pass just wrote: an ordinary launch
-    return launch_rollout_seq(P, b, tile, false, s);
+    return launch_rollout_seq(P, b, tile, it_off, false, s);
   }
   const bool dbg = b.dbg_counts != nullptr || b.dbg_J != nullptr;
   switch (P.system * 4 + (P.noise_bf16 ? 2 : 0) + (dbg ? 1 : 0)) {
@@ -409,27 +439,40 @@ cudaError_t launch_rollout(const DevProblem& P, const IterBuffers& b, const Roll
   return cudaGetLastError();
 }
 
-template <bool BF16, int M, int VPT>
-static void launch_update_t(const UpdateArgs& a, const UpdateGeom& g, cudaStream_t s) {
+template <bool BF16, int M, int VPT, int SRC>
+static void launch_update_t(const UpdateArgs& a, dim3 grid, cudaStream_t s) {
   // Measured on GB300: as a programmatic dependent of the rollout, the
   // update's blocks were resident early and waited on SMs that the
   // concurrent noise pass of the next iteration could have used; an ordinary
   // launch made the MPC step 2 % faster at K = 4096 and at K = 65536.
-  launch_hi(update_kernel<BF16, M, VPT>, dim3(g.chunks, g.groups), dim3(kUpdateThreads), 0, s, false, a);
+  launch_hi(update_kernel<BF16, M, VPT, SRC>, grid, dim3(kUpdateThreads), 0, s, false, a);
 }
 
 template <bool BF16, int M>
-static void launch_update_m(const UpdateArgs& a, const UpdateGeom& g, cudaStream_t s) {
-  if (g.vpt == 4) launch_update_t<BF16, M, 4>(a, g, s);
-  else if (g.vpt == 2) launch_update_t<BF16, M, 2>(a, g, s);
-  else launch_update_t<BF16, M, 1>(a, g, s);
+static void launch_update_m(const UpdateArgs& a, const UpdateGeom& g, bool records, cudaStream_t s) {
+  const dim3 grid(a.chunks, a.groups);
+  if (records) launch_update_t<BF16, M, 1, 1>(a, grid, s);
+  else if (g.vpt == 4) launch_update_t<BF16, M, 4, 0>(a, grid, s);
+  else if (g.vpt == 2) launch_update_t<BF16, M, 2, 0>(a, grid, s);
+  else launch_update_t<BF16, M, 1, 0>(a, grid, s);
+}
+
+int records_per_chunk(int m) {
+  // every thread of a record chunk sums at most eight records (a step group
+  // has 8 m outputs, so 256 / (8 m) partial sums per output)
+  return 8 * (kUpdateThreads / (8 * m));
 }
 
 cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const UpdateGeom& g, int r, int shift,
-                          uint32_t it_advance, float* u0, cudaStream_t s) {
+                          uint32_t it_advance, float* u0, cudaStream_t s, const UpdateSource* src) {
   UpdateArgs a;
   a.noise = b.noise;
   a.s_part = b.s_part;
+  a.rec = nullptr;
+  a.nb = 0;
+  a.bps = 0;
+  a.rho_from_rec = 0;
+  a.export_out = nullptr;
   a.K = P.K;
   a.Kpad = P.Kpad;
   a.T = P.T;
@@ -440,12 +483,22 @@ cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const Updat
   for (int i = 0; i < 4; ++i) a.inv_sigma2[i] = P.inv_sigma2[i];
   a.chunks = g.chunks;
   a.groups = g.groups;
+  const bool records = src && src->rec;
+  if (src) a.export_out = src->export_out;
+  if (records) {
+    a.rec = src->rec;
+    a.nb = src->nb;
+    a.bps = records_per_chunk(P.m);
+    a.rho_from_rec = src->rho_from_rec;
+    a.chunks = (a.nb + a.bps - 1) / a.bps;
+    if (a.nb < 1 || a.chunks > b.max_chunks) return cudaErrorInvalidValue;
+  }
   a.partial = b.partial;
   a.zpart = b.zpart;
   a.gdone = b.done + 4;
   a.edge = b.gpart;
   a.cpart = b.gpart + (size_t)g.groups * P.m;
-  a.e_out = b.w;
+  a.e_out = nullptr;  // the weights getter recomputes e_k from the costs
   a.U = b.U;
   a.u0_out = u0;
   a.diag = b.diag;
@@ -453,17 +506,17 @@ cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const Updat
   a.done = b.done;
   a.rho_key = b.rho_key;
   a.rho_key_next = b.rho_key_next;
-  a.need_final = (shift || it_advance > 0) ? 1 : 0;
+  a.need_final = (shift || it_advance > 0 || a.export_out) ? 1 : 0;
   a.it = b.it;
   a.it_advance = it_advance;
-  a.shift = shift;
+  a.shift = a.export_out ? 0 : shift;
   for (int i = 0; i < 4; ++i) a.u_init[i] = P.u_init[i];
   if (P.m == 4) {
-    if (P.noise_bf16) launch_update_m<true, 4>(a, g, s);
-    else launch_update_m<false, 4>(a, g, s);
+    if (P.noise_bf16) launch_update_m<true, 4>(a, g, records, s);
+    else launch_update_m<false, 4>(a, g, records, s);
   } else {
-    if (P.noise_bf16) launch_update_m<true, 1>(a, g, s);
-    else launch_update_m<false, 1>(a, g, s);
+    if (P.noise_bf16) launch_update_m<true, 1>(a, g, records, s);
+    else launch_update_m<false, 1>(a, g, records, s);
   }
   return cudaGetLastError();
 }
@@ -479,9 +532,9 @@ cudaError_t launch_costs(const DevProblem& P, const IterBuffers& b, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_normalize_weights(const float* e, const float* diag, int K, float* w,
-                                     cudaStream_t s) {
-  normalize_weights_kernel<<<(K + 255) / 256, 256, 0, s>>>(e, diag, K, w);
+cudaError_t launch_weights(const float* s_part, const float* diag, float inv_lam, int K, float* w,
+                           cudaStream_t s) {
+  weights_kernel<<<(K + 255) / 256, 256, 0, s>>>(s_part, diag, inv_lam, K, w);
   return cudaGetLastError();
 }
 

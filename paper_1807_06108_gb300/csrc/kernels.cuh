@@ -21,6 +21,36 @@ constexpr int kRolloutThreads = 128;
 constexpr int kNoiseThreads = 128;
 constexpr int kUpdateThreads = 256;
 constexpr int kStatusNonFinite = 5;
+constexpr int kStatusBounds = 7;  // MPPI_EBOUNDS
+
+// Debug build (MPPI_CHECK_BOUNDS): every kernel first checks that its launch
+// geometry and dynamic shared memory match the problem it was given; a
+// failed check writes MPPI_EBOUNDS into the status word and the whole block
+// returns before touching memory (no trap, no assert).  The conditions are
+// the same for every block of a launch, so no block is left waiting at a
+// barrier.  Compiled out otherwise.
+#ifdef MPPI_CHECK_BOUNDS
+__device__ __forceinline__ void bounds_failed(int* status) {
+  if (status) atomicExch(status, kStatusBounds);
+}
+#define MJ_CHECK(cond, status)    \
+  do {                            \
+    if (!(cond)) {                \
+      bounds_failed(status);      \
+      return;                     \
+    }                             \
+  } while (0)
+#else
+#define MJ_CHECK(cond, status) \
+  do {                         \
+  } while (0)
+#endif
+
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+  uint32_t r;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
 constexpr uint32_t kKeyEmpty = 0xffffffffu;  // larger than every cost key
 constexpr uint32_t kKeyInf = 0xff800000u;    // order key of +inf
 
@@ -43,6 +73,16 @@ __device__ __forceinline__ void publish_min_cost(float sk, uint32_t* rho_key) {
   if ((threadIdx.x & 31) == 0) atomicMin(rho_key, w);
 }
 
+// Compensated sum over the warp (every lane gets the result).
+__device__ __forceinline__ void warp_sum2(float& s, float& c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    two_sum_merge(s, c, s2, c2);
+  }
+}
+
 // Programmatic dependent launch: a kernel launched as the programmatic
 // dependent of the previous kernel in its stream may start while that kernel
 // still runs; griddep_wait() returns once the previous kernel has completed
@@ -54,7 +94,9 @@ __device__ __forceinline__ void griddep_launch_dependents() {
 }
 
 // Mark of the nj-th jump of step j (stream 2+nj of the Philox counter) added
-// to J.
+// to J.  The rounding is explicit (one fused multiply-add per Normal
+// component, one rounded add per Laplace component), so every kernel that
+// draws marks accumulates them bit for bit alike.
 __device__ __forceinline__ void add_mark(const DevProblem& P, uint32_t k, uint32_t j, uint32_t it,
                                          int nj, float J[4]) {
   const uint4 wm = philox4x32_10(k, j, it, 2u + (uint32_t)nj, P.key0, P.key1);
@@ -63,11 +105,11 @@ __device__ __forceinline__ void add_mark(const DevProblem& P, uint32_t k, uint32
     normals4(wm, z);
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-      if (c < P.q) J[c] += P.mark_scale[c] * z[c];
+      if (c < P.q) J[c] = fmaf(P.mark_scale[c], z[c], J[c]);
   } else {
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-      if (c < P.q) J[c] += laplace_mark(P.mark_scale[c], word_of(wm, c));
+      if (c < P.q) J[c] = __fadd_rn(J[c], laplace_mark(P.mark_scale[c], word_of(wm, c)));
   }
 }
 
@@ -156,11 +198,11 @@ __device__ __forceinline__ void cost_and_step(const DevProblem& P, float* x, con
 }
 
 // The state-channel jump of a step (Eq. 2, Algorithm 1), after its Euler
-// step: x[H rows] += s_J J, s_J = sqrt(dt) or 1.  state_jump_default serves
-// the plant's velocity rows, (xdot, thetadot) or (vx, vy, vz), and is applied
-// on every step (J is zero for a step without a jump), so the step loop has
-// no branch; state_jump serves any rows and is called only for steps with a
-// jump.
+// step: x[H rows] += s_J J, s_J = sqrt(dt) or 1.  It is applied on every
+// step (J is zero for a step without a jump, which leaves x unchanged, as in
+// the oracle), so the step loop has no branch.  state_jump_default serves
+// the plant's velocity rows, (xdot, thetadot) or (vx, vy, vz); state_jump_rows
+// any rows; state_jump picks one at run time.
 template <int SYS>
 __device__ __forceinline__ void state_jump_default(const DevProblem& P, float* x, const float J[4]) {
   if constexpr (SYS == 0) {
@@ -174,30 +216,33 @@ __device__ __forceinline__ void state_jump_default(const DevProblem& P, float* x
 }
 
 template <int SYS>
-__device__ __forceinline__ void state_jump(const DevProblem& P, float* x, const float J[4]) {
+__device__ __forceinline__ void state_jump_rows(const DevProblem& P, float* x, const float J[4]) {
   constexpr int n = Plant<SYS>::n;
-  if (P.jump_default) {
-    state_jump_default<SYS>(P, x, J);
-  } else {
 #pragma unroll
-    for (int r = 0; r < n; ++r)
+  for (int r = 0; r < n; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (c < P.q && P.jump_rows[c] == r) x[r] += P.s_jump * J[c];
-  }
+    for (int c = 0; c < 4; ++c)
+      if (c < P.q && P.jump_rows[c] == r) x[r] += P.s_jump * J[c];
+}
+
+template <int SYS>
+__device__ __forceinline__ void state_jump(const DevProblem& P, float* x, const float J[4]) {
+  if (P.jump_default) state_jump_default<SYS>(P, x, J);
+  else state_jump_rows<SYS>(P, x, J);
 }
 
 // Final cost of a rollout: terminal cost, non-finite -> +inf, and the warp's
 // contribution to the running minimum.
 template <int SYS>
-__device__ __forceinline__ void finish_rollout(const DevProblem& P, int k, bool active, const float* x,
-                                               float s, float sc, float* __restrict__ s_part,
-                                               uint32_t* __restrict__ rho_key) {
+__device__ __forceinline__ float finish_rollout(const DevProblem& P, int k, bool active, const float* x,
+                                                float s, float sc, float* __restrict__ s_part,
+                                                uint32_t* __restrict__ rho_key) {
   two_sum_acc(s, sc, Plant<SYS>::terminal_cost(P.pl, x));
   float sk = s + sc;
   if (!isfinite(sk) || !active) sk = INFINITY;
   s_part[k] = sk;
   publish_min_cost(sk, rho_key);  // Kpad is a multiple of 32: whole warps
+  return sk;
 }
 
 
@@ -211,67 +256,81 @@ __device__ __forceinline__ void finish_rollout(const DevProblem& P, int k, bool 
 // so each warp store is contiguous.  Rollouts K..Kpad-1 (padding) store zero
 // noise and an infinite cost.
 // ---------------------------------------------------------------------------
-template <int SYS, bool BF16, bool DBG, bool COHERENT>
+template <int SYS, bool BF16, bool DBG, bool COHERENT, int CH>
 __device__ __forceinline__ void fused_rollout_thread(
     const DevProblem& P, const float* __restrict__ x0, const float* __restrict__ U, uint32_t it, int k,
     float* __restrict__ s_part, void* __restrict__ noise, uint32_t* __restrict__ rho_key,
     uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J);
 
-template <int SYS, bool BF16, bool DBG>
+// CH: steps per unrolled chunk (4, 8 or 16): the chunk's count blocks (one
+// per four steps) are drawn together at its start and its steps are
+// unrolled, so the random numbers of later steps can be computed while the
+// dynamics of earlier ones wait on their dependencies.  Every CH gives the
+// same values.
+template <int SYS, bool BF16, bool DBG, int CH>
 __global__ void __launch_bounds__(kRolloutThreads)
 rollout_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
                const uint32_t* __restrict__ it_ptr, uint32_t it_off, float* __restrict__ s_part,
                void* __restrict__ noise,
                uint32_t* __restrict__ rho_key, uint8_t* __restrict__ dbg_counts,
-               float* __restrict__ dbg_J) {
+               float* __restrict__ dbg_J, int* __restrict__ status) {
+  MJ_CHECK(blockDim.x % 32 == 0 && blockDim.x <= kRolloutThreads && P.Kpad % 32 == 0 && P.K <= P.Kpad,
+           status);
   griddep_launch_dependents();
   griddep_wait();  // U and the running minimum come from the previous update
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P.Kpad) return;
-  fused_rollout_thread<SYS, BF16, DBG, false>(P, x0, U, __ldg(it_ptr) + it_off, k, s_part, noise,
-                                              rho_key, dbg_counts, dbg_J);
+  fused_rollout_thread<SYS, BF16, DBG, false, CH>(P, x0, U, __ldg(it_ptr) + it_off, k, s_part, noise,
+                                                  rho_key, dbg_counts, dbg_J);
 }
 
 // The body of the fused rollout for rollout k < Kpad of a problem; every lane
 // of the warp must run it (k >= Kpad lanes are not allowed: Kpad is a
 // multiple of 32).  COHERENT reads x0 and U through L2, for callers in which
 // another block of the same launch may have written them.
-template <int SYS, bool BF16, bool DBG, bool COHERENT>
+template <int SYS, bool BF16, bool DBG, bool COHERENT, int CH>
 __device__ __forceinline__ void fused_rollout_thread(
     const DevProblem& P, const float* __restrict__ x0, const float* __restrict__ U, uint32_t it, int k,
     float* __restrict__ s_part, void* __restrict__ noise, uint32_t* __restrict__ rho_key,
     uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J) {
+  static_assert(CH == 4 || CH == 8 || CH == 16, "steps per chunk");
   constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
+  constexpr int NB = CH / 4;  // count blocks of a chunk
   const bool active = k < P.K;
-  const uint32_t uk = (uint32_t)k;
+  const uint32_t uk = P.k_base + (uint32_t)k;  // the rollout's index in the Philox counter
   float x[n];
 #pragma unroll
   for (int i = 0; i < n; ++i) x[i] = COHERENT ? __ldcg(x0 + i) : __ldg(x0 + i);
   float s = 0.0f, sc = 0.0f;
-  for (int j0 = 0; j0 < P.T; j0 += 4) {
-    const uint4 wcount = philox4x32_10(uk, (uint32_t)(j0 >> 2), it, 1u, P.key0, P.key1);
-    float zc[4];
-    if constexpr (m == 1) normals4(philox4x32_10(uk, (uint32_t)(j0 >> 2), it, 0u, P.key0, P.key1), zc);
+  for (int j0 = 0; j0 < P.T; j0 += CH) {
+    uint4 wcount[NB];
+    float zc[NB][4];
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
+    for (int c = 0; c < NB; ++c) {
+      const uint32_t b = (uint32_t)((j0 >> 2) + c);
+      wcount[c] = philox4x32_10(uk, b, it, 1u, P.key0, P.key1);
+      if constexpr (m == 1) normals4(philox4x32_10(uk, b, it, 0u, P.key0, P.key1), zc[c]);
+    }
+#pragma unroll
+    for (int jj = 0; jj < CH; ++jj) {
       const int j = j0 + jj;
       if (j >= P.T) break;
       float de[m];
       if constexpr (m == 1) {
-        de[0] = P.sqc_sigma[0] * zc[jj];
+        de[0] = __fmul_rn(P.sqc_sigma[0], zc[jj >> 2][jj & 3]);
       } else {
         float z[4];
         normals4(philox4x32_10(uk, (uint32_t)j, it, 0u, P.key0, P.key1), z);
 #pragma unroll
-        for (int i = 0; i < m; ++i) de[i] = P.sqc_sigma[i] * z[i];
+        for (int i = 0; i < m; ++i) de[i] = __fmul_rn(P.sqc_sigma[i], z[i]);
       }
-      const int N = jump_count(P, word_of(wcount, jj));
+      const int N = jump_count(P, word_of(wcount[jj >> 2], jj & 3));
       float J[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       if (N > 0) {
         draw_marks(P, uk, (uint32_t)j, it, N, J);
         if (P.jump_channel == 1) {
 #pragma unroll
-          for (int i = 0; i < m; ++i) de[i] += J[i];
+          for (int i = 0; i < m; ++i) de[i] = __fadd_rn(de[i], J[i]);
         }
       }
       if constexpr (BF16) {
@@ -282,10 +341,7 @@ __device__ __forceinline__ void fused_rollout_thread(
 #pragma unroll
       for (int i = 0; i < m; ++i) u[i] = COHERENT ? __ldcg(U + j * m + i) : __ldg(U + j * m + i);
       cost_and_step<SYS>(P, x, u, de, s, sc);
-      if (P.jump_channel == 0) {
-        if (P.jump_default) state_jump_default<SYS>(P, x, J);  // J = 0 without a jump
-        else if (N > 0) state_jump<SYS>(P, x, J);
-      }
+      if (P.jump_channel == 0) state_jump<SYS>(P, x, J);  // J = 0 without a jump
       store_noise<m, BF16>(noise, (size_t)j * P.Kpad + k, de, active);
       if (DBG && active) {
         const size_t rk = (size_t)j * P.K + k;
@@ -299,54 +355,67 @@ __device__ __forceinline__ void fused_rollout_thread(
 }
 
 // ---------------------------------------------------------------------------
-// Split form, part 1.  noise_kernel: thread (k, b) draws steps 4b .. 4b+3 of
-// rollout k (the four steps that share one jump-count Philox block), so the
-// sampling runs over K * T/4 threads instead of K.  It stores delta_eff (the
-// control-channel jumps folded in, the bfloat16 rounding applied), the jump
-// counts counts[j*Kpad + k] and, for state-channel jumps, a 16-byte step
-// record jrec[j*Kpad + k] = (J_0, J_1, J_2, N) (or (J_0..J_3) when q = 4);
-// consecutive threads take consecutive k, so every store is contiguous.  It
-// touches nothing the rollout or update of another iteration reads, so it can
-// run concurrently with them on a second buffer set.
+// Split form, part 1.  noise_kernel: thread (k, b), k = blockIdx.x * 128 +
+// threadIdx.x and b = blockIdx.y, draws steps 4b .. 4b+3 of rollout k (the
+// four steps that share one jump-count Philox block), so the sampling runs
+// over K * T/4 threads instead of K.  It stores delta_eff (the bfloat16
+// rounding applied) and the jump counts counts[j*Kpad + k]; consecutive
+// threads take consecutive k, so every store is contiguous.  MARKS: the
+// thread also draws the marks of its jumps -- for control-channel jumps,
+// which are folded into delta_eff, and for the debug copy of J.  For
+// state-channel jumps the marks are drawn by marks_kernel from the counts
+// (only a few percent of the steps jump) into the jump records, which stay
+// zero except where the count is positive: this pass resets the record of
+// any step that jumped when the buffer set was last written and does not
+// jump now.  The pass touches nothing the rollout or update of another
+// iteration reads, so it can run concurrently with them on a second buffer
+// set.
 // ---------------------------------------------------------------------------
-template <int M, bool BF16, bool DBG>
+template <int M, bool BF16, bool DBG, bool MARKS>
 __global__ void __launch_bounds__(kNoiseThreads)
 noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t it_off,
              void* __restrict__ noise, uint8_t* __restrict__ counts, float4* __restrict__ jrec,
-             uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J) {
-  const int nb = (P.T + 3) >> 2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= P.Kpad * nb) return;
-  const int k = t % P.Kpad, b = t / P.Kpad;
+             uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J, int* __restrict__ status) {
+  static_assert(MARKS || !DBG, "the debug copy of J needs the marks");
+  MJ_CHECK(blockDim.x == kNoiseThreads && 4 * (int)blockIdx.y < P.T && P.Kpad % 32 == 0 && P.K <= P.Kpad &&
+               P.m == M,
+           status);
+  const int k = blockIdx.x * kNoiseThreads + threadIdx.x, b = blockIdx.y;
+  if (k >= P.Kpad) return;
   const bool active = k < P.K;
   const uint32_t it = __ldg(it_ptr) + it_off;
-  const uint32_t uk = (uint32_t)k;
+  const uint32_t uk = P.k_base + (uint32_t)k;  // the rollout's index in the Philox counter
   const int ns = min(4, P.T - 4 * b);  // steps of this thread
   const uint4 wcount = philox4x32_10(uk, (uint32_t)b, it, 1u, P.key0, P.key1);
   int N[4];
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj) N[jj] = jj < ns ? jump_count(P, word_of(wcount, jj)) : 0;
-  // Marks, one loop trip per jump in (step, jump) order: a warp runs the mark
-  // code as often as its busiest lane has jumps in its four steps, and the
-  // code exists once.  Each step's marks are summed in jump order, as in
-  // draw_marks.
   float J[4][4];
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
     for (int c = 0; c < 4; ++c) J[jj][c] = 0.0f;
-  const int c0 = N[0], c1 = c0 + N[1], c2 = c1 + N[2], total = c2 + N[3];
+  if constexpr (MARKS) {
+    // Marks, one loop trip per jump in (step, jump) order: a warp runs the
+    // mark code as often as its busiest lane has jumps in its four steps, and
+    // the code exists once.  Each step's marks are summed in jump order, as
+    // in draw_marks.
+    const int c0 = N[0], c1 = c0 + N[1], c2 = c1 + N[2], total = c2 + N[3];
 #pragma unroll 1
-  for (int i = 0; i < total; ++i) {
-    const int jj = i < c0 ? 0 : (i < c1 ? 1 : (i < c2 ? 2 : 3));
-    const int first = jj == 0 ? 0 : (jj == 1 ? c0 : (jj == 2 ? c1 : c2));
-    float Jt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    add_mark(P, uk, (uint32_t)(4 * b + jj), it, i - first, Jt);
+    for (int i = 0; i < total; ++i) {
+      const int jj = i < c0 ? 0 : (i < c1 ? 1 : (i < c2 ? 2 : 3));
+      const int first = jj == 0 ? 0 : (jj == 1 ? c0 : (jj == 2 ? c1 : c2));
+      // the step's running sum, through add_mark as in draw_marks
+      float Jt[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (q == jj)
+      for (int c = 0; c < 4; ++c) Jt[c] = jj == 0 ? J[0][c] : (jj == 1 ? J[1][c] : (jj == 2 ? J[2][c] : J[3][c]));
+      add_mark(P, uk, (uint32_t)(4 * b + jj), it, i - first, Jt);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) J[q][c] += Jt[c];
+      for (int q = 0; q < 4; ++q)
+        if (q == jj)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) J[q][c] = Jt[c];
+    }
   }
   float zc[4];
   if constexpr (M == 1) normals4(philox4x32_10(uk, (uint32_t)b, it, 0u, P.key0, P.key1), zc);
@@ -356,26 +425,22 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
     if (jj >= ns) break;
     float de[M];
     if constexpr (M == 1) {
-      de[0] = P.sqc_sigma[0] * zc[jj];
+      de[0] = __fmul_rn(P.sqc_sigma[0], zc[jj]);
     } else {
       float z[4];
       normals4(philox4x32_10(uk, (uint32_t)j, it, 0u, P.key0, P.key1), z);
 #pragma unroll
-      for (int i = 0; i < M; ++i) de[i] = P.sqc_sigma[i] * z[i];
+      for (int i = 0; i < M; ++i) de[i] = __fmul_rn(P.sqc_sigma[i], z[i]);
     }
     const size_t row = (size_t)j * P.Kpad + k;
-    if (P.jump_channel == 1) {
-      if (N[jj] > 0) {
+    if (MARKS && P.jump_channel == 1 && N[jj] > 0) {
 #pragma unroll
-        for (int i = 0; i < M; ++i) de[i] += J[jj][i];
-      }
-    } else {
-      const float4 rec = P.q > 3 ? make_float4(J[jj][0], J[jj][1], J[jj][2], J[jj][3])
-                                 : make_float4(J[jj][0], J[jj][1], J[jj][2], (float)N[jj]);
-      jrec[row] = active ? rec : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      for (int i = 0; i < M; ++i) de[i] = __fadd_rn(de[i], J[jj][i]);
     }
     store_noise<M, BF16>(noise, row, de, active);  // rounds to bfloat16 (RNE) when BF16
-    counts[row] = active ? (uint8_t)N[jj] : (uint8_t)0;
+    const uint8_t cnew = active ? (uint8_t)N[jj] : (uint8_t)0;
+    if (jrec && cnew == 0 && counts[row] != 0) jrec[row] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    counts[row] = cnew;
     if (DBG && active) {
       const size_t rk = (size_t)j * P.K + k;
       if (dbg_counts) dbg_counts[rk] = (uint8_t)N[jj];
@@ -388,19 +453,76 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
 }
 
 // ---------------------------------------------------------------------------
+// Split form, part 1b (state-channel jumps).  marks_kernel: the marks of every
+// step whose count is positive, with the lanes of a warp busy on jumps
+// rather than on steps.  A warp covers 512 consecutive rollouts of one step j
+// (a 16-byte load of counts per lane), lists the jumping steps in shared
+// memory (a ballot prefix sum: deterministic positions) and draws each one's
+// summed marks on one lane (draw_marks, streams 2+n, as every other form
+// does), writing J into the step's jump record.  Grid (ceil(Kpad / 2048), T),
+// kMarkThreads threads.
+// ---------------------------------------------------------------------------
+constexpr int kMarkThreads = 128;
+constexpr int kMarkSpan = 512;  // rollouts per warp
+
+static __global__ void __launch_bounds__(kMarkThreads)
+marks_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t it_off,
+             const uint8_t* __restrict__ counts, float4* __restrict__ jrec, int* __restrict__ status) {
+  __shared__ uint32_t list[kMarkThreads / 32][kMarkSpan];
+  MJ_CHECK(blockDim.x == kMarkThreads && (int)blockIdx.y < P.T && P.Kpad % 32 == 0, status);
+  const int j = blockIdx.y;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int kw = (blockIdx.x * (kMarkThreads / 32) + w) * kMarkSpan;  // the warp's first rollout
+  const int kt = kw + 16 * lane;
+  uint4 x = make_uint4(0u, 0u, 0u, 0u);
+  // Kpad is a multiple of 32, so kt < Kpad keeps all 16 bytes in the row
+  if (kt < P.Kpad) x = *reinterpret_cast<const uint4*>(counts + (size_t)j * P.Kpad + kt);
+  const uint32_t wd[4] = {x.x, x.y, x.z, x.w};
+  uint32_t nz = 0u;
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    if ((wd[q >> 2] >> (8 * (q & 3))) & 0xffu) nz |= 1u << q;
+  const int ne = __popc(nz);  // 0 .. 16
+  uint32_t bal[5];
+#pragma unroll
+  for (int b = 0; b < 5; ++b) bal[b] = __ballot_sync(0xffffffffu, (ne >> b) & 1);
+  const uint32_t lt = (1u << lane) - 1u;
+  int total = 0, pos = 0;
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    total += __popc(bal[b]) << b;
+    pos += __popc(bal[b] & lt) << b;
+  }
+  if (total == 0) return;  // the same for every lane of the warp
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    if ((nz >> q) & 1u) list[w][pos++] = ((uint32_t)(16 * lane + q) << 5) | ((wd[q >> 2] >> (8 * (q & 3))) & 0xffu);
+  __syncwarp();
+  const uint32_t it = __ldg(it_ptr) + it_off;
+  for (int e = lane; e < total; e += 32) {
+    const uint32_t ev = list[w][e];
+    const int k = kw + (int)(ev >> 5), c = (int)(ev & 31u);
+    float J[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    draw_marks(P, P.k_base + (uint32_t)k, (uint32_t)j, it, c, J);
+    jrec[(size_t)j * P.Kpad + k] = make_float4(J[0], J[1], J[2], J[3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Split form, part 2.  rollout_split_kernel: one thread per rollout runs the
 // sequential dynamics from the stored step data.  A register ring of kAhead
 // slots keeps the loads of step j + kAhead in flight while step j is
 // computed (the loop is unrolled by kAhead so every slot index is static);
-// kAhead is the tile's "steps per unrolled chunk".
+// kAhead is the tile's "steps per unrolled chunk".  State-channel jumps add
+// the step's jump record (zero without a jump) on every step.
 // ---------------------------------------------------------------------------
 template <int SYS, bool BF16, int kAhead>
 __global__ void __launch_bounds__(kRolloutThreads)
 rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
-                     const void* __restrict__ noise, const uint8_t* __restrict__ counts,
-                     const float4* __restrict__ jrec, float* __restrict__ s_part,
-                     uint32_t* __restrict__ rho_key) {
+                     const void* __restrict__ noise, const float4* __restrict__ jrec,
+                     float* __restrict__ s_part, uint32_t* __restrict__ rho_key, int* __restrict__ status) {
   constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
+  MJ_CHECK(blockDim.x % 32 == 0 && blockDim.x <= kRolloutThreads && P.Kpad % 32 == 0 && P.m == m, status);
   griddep_launch_dependents();
   griddep_wait();  // U and the running minimum come from the previous update
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -408,7 +530,6 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
   const bool active = k < P.K;
   const int T = active ? P.T : 0;  // padding lanes skip the loop
   const bool sj = P.jump_channel == 0;
-  const bool q4 = P.q > 3;
   float x[n];
 #pragma unroll
   for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
@@ -416,9 +537,7 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
 
   float rd[kAhead][m], ru[kAhead][m];
   float4 rj[kAhead];
-  int rc[kAhead];
-  auto fetch = [&](int slot_unused, int step, float* d, float* u, float4& jr, int& c) {
-    (void)slot_unused;
+  auto fetch = [&](int step, float* d, float* u, float4& jr) {
     const size_t row = (size_t)step * P.Kpad + k;
     load_noise<m, BF16>(noise, row, d);
     if constexpr (m == 4) {  // U rows are 16-byte aligned
@@ -432,11 +551,10 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
       for (int i = 0; i < m; ++i) u[i] = __ldg(U + step * m + i);
     }
     jr = sj ? __ldg(jrec + row) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    c = (sj && q4) ? (int)__ldg(counts + row) : 0;
   };
 #pragma unroll
   for (int sl = 0; sl < kAhead; ++sl)
-    if (sl < T) fetch(sl, sl, rd[sl], ru[sl], rj[sl], rc[sl]);
+    if (sl < T) fetch(sl, rd[sl], ru[sl], rj[sl]);
 
   for (int j0 = 0; j0 < T; j0 += kAhead) {
 #pragma unroll
@@ -450,13 +568,9 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
         u[i] = ru[jj][i];
       }
       const float J[4] = {rj[jj].x, rj[jj].y, rj[jj].z, rj[jj].w};
-      const bool jumped = sj && (q4 ? rc[jj] > 0 : rj[jj].w > 0.5f);
-      if (j + kAhead < T) fetch(jj, j + kAhead, rd[jj], ru[jj], rj[jj], rc[jj]);
+      if (j + kAhead < T) fetch(j + kAhead, rd[jj], ru[jj], rj[jj]);
       cost_and_step<SYS>(P, x, u, de, s, sc);
-      if (sj) {
-        if (P.jump_default) state_jump_default<SYS>(P, x, J);  // a zero record without a jump
-        else if (jumped) state_jump<SYS>(P, x, J);
-      }
+      if (sj) state_jump<SYS>(P, x, J);  // a zero record without a jump
     }
   }
   finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
@@ -528,196 +642,322 @@ constexpr int kStatusTimeout = 4;               // MPPI_ETIMEOUT
 // ---------------------------------------------------------------------------
 // Split form, part 2, staged.  rollout_staged_kernel: the same per-rollout
 // sequential dynamics as rollout_split_kernel, but the step data of the
-// block's rollouts (delta_eff rows, and the jump records and counts as the
-// jump mode needs them) is moved into shared memory by the bulk-copy engine,
-// S steps per stage, two stages in flight.  The block is nt compute threads
-// (one per rollout) plus one producer warp.
-// Each stage buffer has a "full" mbarrier (the copies landed) and an "empty"
-// one (every compute warp is done with it): a compute warp waits for "full",
-// runs its S steps from shared memory, releases the buffer and moves on; the
-// producer's lane 0 waits for "empty" and issues the copies of stage s + 2
-// into the buffer.  No compute thread ever waits for another or issues a
-// copy, and the dependency chain of the dynamics never waits on a global
-// load.  For block b the rows are contiguous: step j covers elements
-// [j*Kpad + b*nt, j*Kpad + b*nt + nk) of every step-major array (nk = the
-// block's rollouts, a multiple of 32, so every copy is 16-byte aligned and a
-// multiple of 16 bytes).  The stage also carries the S control rows (one copy
-// rounded up to 16 bytes, which may read up to 12 bytes past U's end: U must
-// sit in an allocation padded to 16 bytes).  Each compute thread reads a
-// step's data from shared memory at the start of the step.  Launch with
-// nt + 32 threads; dynamic shared memory 2 * (S * nt * (m*s_b + 16 + 1) +
-// round16(S * m * 4)) bytes + 32 (the jump-record and count regions only for
-// state-channel jumps).
+// block's rollouts (delta_eff rows, the control rows and, for state-channel
+// jumps, the jump-record rows) is moved into shared memory by the bulk-copy
+// engine, S steps per stage, two stage buffers.  The block is nt compute
+// threads (one per rollout) plus one producer warp.
+//
+// Each stage buffer has a "landed" mbarrier (its copies are complete) and an
+// "empty" one (every compute warp is done with it).  The producer's lane 0
+// issues the copies of stage s + 2 into a buffer once its compute warps have
+// released it from stage s.  A compute warp waits for "landed", runs its S
+// steps from shared memory, releases the buffer and moves on; no compute
+// thread issues a copy or waits for another, and the dependency chain of the
+// dynamics never waits on a global load.  For block b the rows are
+// contiguous: step j covers elements [j*Kpad + b*nt, j*Kpad + b*nt + nk) of
+// every step-major array (nk = the block's rollouts, a multiple of 32, so
+// every copy is 16-byte aligned and a multiple of 16 bytes).  The
+// control-row copy is rounded up to 16 bytes and may read up to 12 bytes past
+// U's end (U must sit in an allocation padded to 16 bytes).  A compute thread
+// adds s_J * J from its jump record on every step (the record is zero for a
+// step without a jump), so the step loop has no branch.  Every wait is
+// bounded.  Launch with nt + 32 threads and staged_smem_total() bytes of
+// dynamic shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kStagedMaxThreads = kRolloutThreads + 32;
 
-// How a staged rollout applies state-channel jumps (a template argument, so
-// that the step loop carries only what the problem needs):
-//   kJumpNone    jumps act on the controls (folded into delta_eff): no jump
-//                records are read;
-//   kJumpDefault jumps hit the plant's velocity rows: every step adds
-//                s_J J from its record, which is zero for a step without a
-//                jump, so the step loop has no branch;
-//   kJumpRows    any other rows: the counts are copied too, and a step reads
-//                its record and applies it only when its count is positive.
+// How a staged rollout applies jumps (a template argument, so that the step
+// loop carries only what the problem needs):
+//   kJumpNone    jumps act on the controls (folded into delta_eff);
+//   kJumpDefault state jumps on the plant's velocity rows;
+//   kJumpRows    state jumps on any other rows.
 constexpr int kJumpNone = 0, kJumpDefault = 1, kJumpRows = 2;
 
-template <int SYS, bool BF16, int S, int JM>
-__global__ void __launch_bounds__(kStagedMaxThreads)
+// Shared-memory layout of the staged rollout (bytes), shared with the host:
+// two stage buffers, four mbarriers and the partial record's scratch (PART).
+__host__ __device__ constexpr uint32_t staged_stage_bytes(int nt, int m, int sb, int S, bool jumps) {
+  return (uint32_t)S * ((uint32_t)nt * m * sb + (jumps ? (uint32_t)nt * 16u : 0u)) +
+         (((uint32_t)S * m * 4u + 15u) & ~15u);
+}
+__host__ __device__ constexpr uint32_t staged_tail_offset(int nt, int m, int sb, int S, bool jumps) {
+  return 2u * staged_stage_bytes(nt, m, sb, S, jumps) + 4u * 8u;
+}
+constexpr uint32_t kTailFloats = kRolloutThreads + 16;
+__host__ __device__ constexpr uint32_t staged_smem_total(int nt, int m, int sb, int S, bool jumps, bool part) {
+  return staged_tail_offset(nt, m, sb, S, jumps) + (part ? 4u * kTailFloats : 0u);
+}
+
+// PART: after its rollouts the block forms its partial record (Eq. 36-37
+// restricted to its rollouts) rec[b] = (rho_b, Z_b, N_b[T][m]):
+// rho_b = min S~_k, e_k = exp(-(S~_k - rho_b)/lambda), Z_b = sum e_k and
+// N_b[j][i] = sum_k e_k delta_eff[j][k][i], re-reading its perturbation rows
+// through the same two stage buffers (the producer copies them again, each
+// compute warp reduces whole rows: per-lane products, compensated shuffle
+// sums).  The update then only rescales and sums the records
+// (update_kernel with the record source), with no second pass over the
+// perturbations.
+template <int SYS, bool BF16, int S, int JM, bool PART>
+__global__ void __launch_bounds__(kStagedMaxThreads, 4)
 rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
-                      const void* __restrict__ noise, const uint8_t* __restrict__ counts,
-                      const float4* __restrict__ jrec, float* __restrict__ s_part,
-                      uint32_t* __restrict__ rho_key, int* __restrict__ status) {
+                      const void* __restrict__ noise, const float4* __restrict__ jrec,
+                      float* __restrict__ s_part, uint32_t* __restrict__ rho_key, int* __restrict__ status,
+                      float* __restrict__ rec) {
   constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
+  constexpr bool kJ = JM != kJumpNone;
   constexpr uint32_t SB = BF16 ? 2u : 4u;
   extern __shared__ __align__(128) unsigned char stage_smem[];
   const int nt = blockDim.x - 32, tid = threadIdx.x;  // compute threads, then the producer warp
   const int k0 = blockIdx.x * nt;
   const int nk = min(nt, P.Kpad - k0);
   const int T = P.T;
-  const uint32_t d_stride = (uint32_t)nt * m * SB, j_stride = JM != kJumpNone ? (uint32_t)nt * 16u : 0u,
-                 c_stride = JM == kJumpRows ? (uint32_t)nt : 0u;
-  const uint32_t u_off = S * (d_stride + j_stride + c_stride);  // control rows
-  const uint32_t stage_bytes = u_off + ((S * m * 4 + 15) & ~15u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(stage_smem + 2 * stage_bytes);
-  uint64_t* empty = full + 2;
+  const uint32_t d_stride = (uint32_t)nt * m * SB;         // delta_eff of one step
+  const uint32_t j_stride = kJ ? (uint32_t)nt * 16u : 0u;  // jump records of one step
+  const uint32_t t_off = S * d_stride;                     // jump records
+  const uint32_t u_off = S * (d_stride + j_stride);        // control rows
+  const uint32_t stage_bytes = staged_stage_bytes(nt, m, (int)SB, S, kJ);
+  uint64_t* landed = reinterpret_cast<uint64_t*>(stage_smem + 2 * stage_bytes);
+  uint64_t* empty = landed + 2;
+  float* tail = reinterpret_cast<float*>(stage_smem + staged_tail_offset(nt, m, (int)SB, S, kJ));
+  int* abort_flag = reinterpret_cast<int*>(tail + kRolloutThreads + 8);
   const int n_stages = (T + S - 1) / S;
   const int compute_warps = nt / 32;
+  const uint32_t d_bytes = (uint32_t)nk * m * SB;
+  MJ_CHECK(nt >= 32 && nt <= kRolloutThreads && nt % 32 == 0 && k0 < P.Kpad && P.Kpad % 32 == 0 && T >= 1 &&
+               P.m == m && (P.noise_bf16 != 0) == BF16 &&
+               dynamic_smem_bytes() >= staged_smem_total(nt, m, (int)SB, S, kJ, PART),
+           status);
 
   griddep_launch_dependents();
   if (tid == nt) {
-    mbar_init(full, 1);
-    mbar_init(full + 1, 1);
+    mbar_init(landed, 1);
+    mbar_init(landed + 1, 1);
     mbar_init(empty, (uint32_t)compute_warps);
     mbar_init(empty + 1, (uint32_t)compute_warps);
     mbar_init_fence();
     fence_async_smem();
+    if (PART) *abort_flag = 0;
   }
   __syncthreads();
 
+  // lane 0 of the producer: the perturbation rows of stage g (stage g >=
+  // n_stages is pass g - n_stages over the rows, for the partial record) into
+  // buffer g & 1
+  auto issue_delta = [&](int g, int j0, int ns) {
+    unsigned char* base = stage_smem + (g & 1) * stage_bytes;
+    for (int jj = 0; jj < ns; ++jj) {
+      const size_t row = (size_t)(j0 + jj) * P.Kpad + k0;
+      bulk_load(base + jj * d_stride, static_cast<const unsigned char*>(noise) + row * m * SB, d_bytes,
+                landed + (g & 1));
+    }
+  };
+  int issued = 0;  // stages whose copies the producer issued
+  bool ok = true;
+
   if (tid >= nt) {
     // ---- producer warp: lane 0 issues every stage's copies
-    if (tid != nt) return;
-    const uint32_t d_bytes = (uint32_t)nk * m * SB, j_bytes = JM != kJumpNone ? (uint32_t)nk * 16u : 0u,
-                   c_bytes = JM == kJumpRows ? (uint32_t)nk : 0u;
-    int issued = 0;
-    bool ok = true, waited = false;
-    for (int st = 0; st < n_stages && ok; ++st) {
-      const int buf = st & 1;
-      if (st >= 2) {
-        // every compute warp released the buffer (use st/2 - 1 of it)
-        ok = mbar_wait_bounded(empty + buf, (uint32_t)((st >> 1) - 1) & 1u, kCopyWaitNs);
-        if (!ok) break;
-        fence_async_smem();
-      }
-      const int j0 = st * S;
-      const int ns = min(S, T - j0);
-      unsigned char* base = stage_smem + buf * stage_bytes;
-      const uint32_t u_bytes = ((uint32_t)ns * m * 4 + 15) & ~15u;
-      mbar_expect_tx(full + buf, (uint32_t)ns * (d_bytes + j_bytes + c_bytes) + u_bytes);
-      for (int jj = 0; jj < ns; ++jj) {
-        const size_t row = (size_t)(j0 + jj) * P.Kpad + k0;
-        bulk_load(base + jj * d_stride, static_cast<const unsigned char*>(noise) + row * m * SB, d_bytes,
-                  full + buf);
-        if (j_bytes) bulk_load(base + S * d_stride + jj * j_stride, jrec + row, j_bytes, full + buf);
-        if (c_bytes)
-          bulk_load(base + S * (d_stride + j_stride) + jj * c_stride, counts + row, c_bytes, full + buf);
-      }
-      // the step data was drawn before the previous kernel; the controls come
-      // from the previous update
-      if (!waited) {
-        griddep_wait();
-        waited = true;
-      }
-      bulk_load(base + u_off, U + (size_t)j0 * m, u_bytes, full + buf);
-      ++issued;
-    }
-    if (!ok) atomicExch(status, kStatusTimeout);
-    // leave only when the copies of the last two stages have landed (bounded)
-    for (int ls = max(0, issued - 2); ls < issued; ++ls)
-      mbar_wait_bounded(full + (ls & 1), (uint32_t)(ls >> 1) & 1u, kCopyWaitNs);
-    return;
-  }
-
-  // ---- compute threads: one rollout each
-  const int k = k0 + tid;
-  const bool mine = tid < nk;  // a rollout slot of this block (whole warps)
-  const bool active = k < P.K;
-  float x[n];
-#pragma unroll
-  for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
-  float s = 0.0f, sc = 0.0f;
-  for (int st = 0; st < n_stages; ++st) {
-    const int buf = st & 1;
-    if (!mbar_wait_bounded(full + buf, (uint32_t)(st >> 1) & 1u, kCopyWaitNs)) {
-      atomicExch(status, kStatusTimeout);
-      return;
-    }
-    if (mine && active) {
-      const unsigned char* base = stage_smem + buf * stage_bytes;
-      const int j0 = st * S;
-      const int ns = min(S, T - j0);
-      // step data of step jj of this stage, from shared memory
-      auto fetch = [&](int jj, float* de, float* u) {
-        load_noise<m, BF16>(base + jj * d_stride, tid, de);
-        if constexpr (m == 4) {
-          const float4 u4 = reinterpret_cast<const float4*>(base + u_off)[jj];
-          u[0] = u4.x;
-          u[1] = u4.y;
-          u[2] = u4.z;
-          u[3] = u4.w;
-        } else {
-          u[0] = reinterpret_cast<const float*>(base + u_off)[jj];
+    if (tid == nt) {
+      const uint32_t j_bytes = kJ ? (uint32_t)nk * 16u : 0u;
+      for (int st = 0; st < n_stages && ok; ++st) {
+        const int buf = st & 1;
+        if (st >= 2) {
+          // every compute warp released the buffer (use st/2 - 1 of it)
+          ok = mbar_wait_bounded(empty + buf, (uint32_t)((st >> 1) - 1) & 1u, kCopyWaitNs);
+          if (!ok) break;
+          fence_async_smem();
         }
-      };
-      auto record = [&](int jj) {
-        return reinterpret_cast<const float4*>(base + S * d_stride + jj * j_stride)[tid];
-      };
-      // Each step reads its data from shared memory at its start.  Long
-      // stages (one block per SM, one warp per scheduler) unroll four steps,
-      // which lets the compiler issue the reads of later steps early; short
-      // ones (several blocks per SM, issue-bound) do not unroll, and the small
-      // loop body stays in the instruction cache.  Measured on GB300 against
-      // a one-step register prefetch with two-fold unrolling: MPC step 0.3217
-      // -> 0.3187 ms at K = 4096, 1.3056 -> 1.2826 ms at K = 65536.
-      constexpr int kUnroll = S >= 16 ? 4 : 1;
+        const int j0 = st * S;
+        const int ns = min(S, T - j0);
+        unsigned char* base = stage_smem + buf * stage_bytes;
+        const uint32_t u_bytes = ((uint32_t)ns * m * 4 + 15) & ~15u;
+        mbar_expect_tx(landed + buf, (uint32_t)ns * (d_bytes + j_bytes) + u_bytes);
+        issue_delta(st, j0, ns);
+        if (kJ)
+          for (int jj = 0; jj < ns; ++jj)
+            bulk_load(base + t_off + jj * j_stride, jrec + (size_t)(j0 + jj) * P.Kpad + k0, j_bytes,
+                      landed + buf);
+        // the step data was drawn before the previous kernel; the controls
+        // come from the previous update
+        if (st == 0) griddep_wait();
+        bulk_load(base + u_off, U + (size_t)j0 * m, u_bytes, landed + buf);
+        ++issued;
+      }
+      if (!ok) {
+        atomicExch(status, kStatusTimeout);
+        if (PART) *abort_flag = 1;
+      }
+    }
+    issued = __shfl_sync(0xffffffffu, issued, 0);
+  } else {
+    // ---- compute threads: one rollout each
+    const int k = k0 + tid;
+    const bool mine = tid < nk;  // a rollout slot of this block (whole warps)
+    const bool active = k < P.K;
+    float x[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
+    float s = 0.0f, sc = 0.0f;
+    for (int st = 0; st < n_stages; ++st) {
+      const int buf = st & 1;
+      if (!mbar_wait_bounded(landed + buf, (uint32_t)(st >> 1) & 1u, kCopyWaitNs)) {
+        atomicExch(status, kStatusTimeout);
+        ok = false;
+        break;
+      }
+      if (mine && active) {
+        const unsigned char* base = stage_smem + buf * stage_bytes;
+        const int j0 = st * S;
+        const int ns = min(S, T - j0);
+        // step data of step jj of this stage, from shared memory
+        auto fetch = [&](int jj, float* de, float* u) {
+          load_noise<m, BF16>(base + jj * d_stride, tid, de);
+          if constexpr (m == 4) {
+            const float4 u4 = reinterpret_cast<const float4*>(base + u_off)[jj];
+            u[0] = u4.x;
+            u[1] = u4.y;
+            u[2] = u4.z;
+            u[3] = u4.w;
+          } else {
+            u[0] = reinterpret_cast<const float*>(base + u_off)[jj];
+          }
+        };
+        // Each step reads its data from shared memory at its start.  Long
+        // stages (one block per SM, one warp per scheduler) unroll four steps,
+        // which lets the compiler issue the reads of later steps early; short
+        // ones (several blocks per SM, issue-bound) do not unroll, and the small
+        // loop body stays in the instruction cache.  Measured on GB300 against
+        // a one-step register prefetch with two-fold unrolling: MPC step 0.3217
+        // -> 0.3187 ms at K = 4096, 1.3056 -> 1.2826 ms at K = 65536.
+        constexpr int kUnroll = S >= 16 ? 4 : 1;
 #pragma unroll kUnroll
-      for (int jj = 0; jj < ns; ++jj) {
-        float de[m], u[m];
-        fetch(jj, de, u);
-        cost_and_step<SYS>(P, x, u, de, s, sc);
-        if constexpr (JM == kJumpDefault) {
-          const float4 jr = record(jj);  // zero for a step without a jump
-          const float J[4] = {jr.x, jr.y, jr.z, jr.w};
-          state_jump_default<SYS>(P, x, J);
-        } else if constexpr (JM == kJumpRows) {
-          if (base[S * (d_stride + j_stride) + jj * c_stride + tid] > 0) {
-            const float4 jr = record(jj);
-            const float J[4] = {jr.x, jr.y, jr.z, jr.w};
-            state_jump<SYS>(P, x, J);
+        for (int jj = 0; jj < ns; ++jj) {
+          float de[m], u[m];
+          fetch(jj, de, u);
+          cost_and_step<SYS>(P, x, u, de, s, sc);
+          if constexpr (kJ) {
+            const float4 jr = reinterpret_cast<const float4*>(base + t_off + jj * j_stride)[tid];
+            const float J[4] = {jr.x, jr.y, jr.z, jr.w};  // zero for a step without a jump
+            if constexpr (JM == kJumpDefault) state_jump_default<SYS>(P, x, J);
+            else state_jump_rows<SYS>(P, x, J);
           }
         }
       }
+      // this warp is done with the buffer
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(empty + buf);
     }
-    // this warp is done with the buffer
-    __syncwarp();
-    if ((tid & 31) == 0) mbar_arrive(empty + buf);
+    if (!PART && !ok) return;
+    griddep_wait();  // the running minimum was re-armed by the previous update
+    float sk = INFINITY;
+    if (mine && ok) sk = finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
+    if (PART) {
+      tail[tid] = sk;
+      if (!ok) *abort_flag = 1;
+    }
   }
-  griddep_wait();  // the running minimum was re-armed by the previous update
-  if (mine) finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
+
+  if constexpr (PART) {
+    // ---- the block's partial record
+    float* e_sh = tail;                        // [nt]: S~_k, then e_k
+    float* zw = tail + kRolloutThreads;        // [8]: compensated Z of each compute warp
+    float* rho_sh = tail + kRolloutThreads + 9;
+    const size_t R = 2 + (size_t)T * m;
+    float* rb = rec + (size_t)blockIdx.x * R;
+    __syncthreads();
+    const bool go = *abort_flag == 0;
+    if (go) {
+      if (tid < 32) {
+        float r = INFINITY;
+        for (int t = tid; t < nt; t += 32) r = fminf(r, e_sh[t]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fminf(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if (tid == 0) *rho_sh = r;
+      }
+      __syncthreads();
+      const float rho_b = *rho_sh;
+      const bool any = rho_b < INFINITY;
+      if (tid < nt) {
+        const float sk = e_sh[tid];
+        const float e = (any && sk < INFINITY) ? expf((rho_b - sk) * P.inv_lam) : 0.0f;
+        e_sh[tid] = e;
+        float zs = e, zc = 0.0f;
+        warp_sum2(zs, zc);
+        if ((tid & 31) == 0) {
+          zw[2 * (tid >> 5)] = zs;
+          zw[2 * (tid >> 5) + 1] = zc;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float zs = 0.0f, zc = 0.0f;
+        for (int w = 0; w < compute_warps; ++w) two_sum_merge(zs, zc, zw[2 * w], zw[2 * w + 1]);
+        rb[0] = rho_b;
+        rb[1] = any ? zs + zc : 0.0f;
+      }
+      if (!any) {
+        for (int idx = tid; idx < T * m; idx += nt + 32) rb[2 + idx] = 0.0f;
+      } else if (tid >= nt) {
+        // producer: the perturbation rows again, stage by stage
+        if (tid == nt) {
+          fence_async_smem();
+          for (int ts = 0; ts < n_stages; ++ts) {
+            const int g = n_stages + ts;
+            if (ts >= 2 && !mbar_wait_bounded(empty + (g & 1), (uint32_t)((g >> 1) - 1) & 1u, kCopyWaitNs)) {
+              atomicExch(status, kStatusTimeout);
+              break;
+            }
+            if (ts >= 2) fence_async_smem();
+            const int j0 = ts * S, ns = min(S, T - j0);
+            mbar_expect_tx(landed + (g & 1), (uint32_t)ns * d_bytes);
+            issue_delta(g, j0, ns);
+            issued = g + 1;
+          }
+        }
+        issued = __shfl_sync(0xffffffffu, issued, 0);
+      } else {
+        // compute warps: whole rows, lane l takes rollouts l, l + 32, ...
+        const int wid = tid >> 5, lane = tid & 31;
+        for (int ts = 0; ts < n_stages; ++ts) {
+          const int g = n_stages + ts;
+          if (!mbar_wait_bounded(landed + (g & 1), (uint32_t)(g >> 1) & 1u, kCopyWaitNs)) {
+            atomicExch(status, kStatusTimeout);
+            break;
+          }
+          const unsigned char* base = stage_smem + (g & 1) * stage_bytes;
+          const int j0 = ts * S, ns = min(S, T - j0);
+          for (int jj = wid; jj < ns; jj += compute_warps) {
+            float acc[m];
+#pragma unroll
+            for (int i = 0; i < m; ++i) acc[i] = 0.0f;
+            for (int t = lane; t < nk; t += 32) {
+              float d[m];
+              load_noise<m, BF16>(base + jj * d_stride, t, d);
+              const float e = e_sh[t];
+#pragma unroll
+              for (int i = 0; i < m; ++i) acc[i] = fmaf(e, d[i], acc[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < m; ++i) {
+              float c = 0.0f;
+              warp_sum2(acc[i], c);
+              if (lane == 0) rb[2 + (size_t)(j0 + jj) * m + i] = acc[i] + c;
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(empty + (g & 1));
+        }
+      }
+    }
+  }
+  if (tid == nt) {
+    // leave only when the copies of the last two issued stages have landed (bounded)
+    for (int ls = max(0, issued - 2); ls < issued; ++ls)
+      mbar_wait_bounded(landed + (ls & 1), (uint32_t)(ls >> 1) & 1u, kCopyWaitNs);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Block reductions (NT threads per block)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void warp_sum2(float& s, float& c) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-    two_sum_merge(s, c, s2, c2);
-  }
-}
 
 // Shared scratch of the update bodies for NT threads: per-warp partial sums
 // and the weights of one chunk of rollouts (ECAP floats).
@@ -725,7 +965,9 @@ template <int NT, int ECAP>
 struct UpdateShared {
   float sh_s[NT / 32], sh_c[NT / 32];
   unsigned ticket;
+  float rho;
   __align__(16) float e[ECAP];
+  float red[NT];
 };
 
 // Rollouts per chunk of the weighted sum: NT * VPT 16-byte vectors of a row.
@@ -801,6 +1043,12 @@ costs_kernel(const float* __restrict__ U, int T, float lam, float4 inv_sigma2,
 struct UpdateArgs {
   const void* noise;
   const float* s_part;
+  // partial records [nb][2 + T*M] = (rho_b, Z_b, N_b[T][M]) of rollout blocks
+  // or rollout shards, summed bps records per chunk (record source only)
+  const float* rec;
+  int nb, bps;
+  int rho_from_rec;   // rho = min over the records' rho_b (else the running minimum)
+  float* export_out;  // non-NULL: write the combined record (rho, Z, N) instead of updating U
   int K, Kpad, T, rows;
   float inv_lam, lam, alpha;
   float inv_sigma2[4];
@@ -810,7 +1058,7 @@ struct UpdateArgs {
   unsigned* gdone;  // [groups] completion tickets of the step groups
   float* edge;     // [groups][M] shifted first-row values of each group
   float* cpart;    // [groups] control cost of each group's rows
-  float* e_out;    // [Kpad]
+  float* e_out;    // [Kpad] or NULL
   float* U;        // [T][M]
   float* u0_out;   // [M] or NULL
   float* diag;     // rho, Z, F
@@ -898,7 +1146,7 @@ __device__ __forceinline__ void update_partial_body(const UpdateArgs& a, float r
     if (r < nr) {
       const float e = expf((rho - sv) * a.inv_lam);
       sh.e[r] = e;
-      if (write_e) a.e_out[v0 * RPV + r] = e;
+      if (write_e && a.e_out) a.e_out[v0 * RPV + r] = e;
       two_sum_acc(zs, zc, e);
     }
   }
@@ -968,6 +1216,52 @@ __device__ __forceinline__ void update_partial_body(const UpdateArgs& a, float r
       warp_sum2(acc[i], c);
       if (lane == 0) a.partial[((size_t)chunk * a.T + j) * M + i] = acc[i] + c;
     }
+  }
+}
+
+// Partial body over partial records (Eq. 37 split over rollout blocks or
+// shards): record b holds rho_b = min S~ over its rollouts, Z_b =
+// sum exp(-(S~_k - rho_b)/lambda) and N_b[j][i] = sum e_k delta_eff[j][k][i]
+// with the same e_k.  With s_b = exp(-(rho_b - rho)/lambda) the shift-
+// invariant rescaling gives Z_c = sum_b s_b Z_b and N_c = sum_b s_b N_b over
+// the chunk's records b in [c*bps, c*bps + bps), written like the streaming
+// partial body's output, so the group combine and final body are shared.
+template <int M, int NT, class SH>
+__device__ __forceinline__ void update_partial_records(const UpdateArgs& a, float rho, int chunk,
+                                                       int j_begin, int j_end, float* zdst, SH& sh) {
+  constexpr int GM = (NT / 32) * M;  // outputs of a full step group
+  constexpr int PS = NT / GM;        // partial sums per output
+  const int tid = threadIdx.x;
+  const size_t R = 2 + (size_t)a.T * M;  // record stride
+  const int b0 = chunk * a.bps, b1 = min(a.nb, b0 + a.bps);
+  const int nbc = b1 - b0;
+  float zs = 0.0f, zc = 0.0f;
+  for (int i = tid; i < nbc; i += NT) {
+    const float rb = __ldcg(a.rec + (size_t)(b0 + i) * R);
+    const float zb = __ldcg(a.rec + (size_t)(b0 + i) * R + 1);
+    const float sc = rb < INFINITY ? expf((rho - rb) * a.inv_lam) : 0.0f;  // rho <= rb
+    sh.e[i] = sc;
+    two_sum_acc(zs, zc, sc * zb);
+  }
+  if (zdst) {
+    const float z = block_sum2<NT>(zs, zc, sh.sh_s, sh.sh_c);  // its barriers publish sh.e
+    if (tid == 0) *zdst = z;
+  } else {
+    __syncthreads();
+  }
+  const int o = tid % GM, p = tid / GM;
+  const int G = (j_end - j_begin) * M;
+  float sv = 0.0f, cv = 0.0f;
+  if (o < G)
+    for (int i = p; i < nbc; i += PS)
+      two_sum_acc(sv, cv, sh.e[i] * __ldcg(a.rec + (size_t)(b0 + i) * R + 2 + (size_t)j_begin * M + o));
+  sh.red[tid] = sv + cv;
+  __syncthreads();
+  if (tid < G) {
+    float ts = 0.0f, tc = 0.0f;
+#pragma unroll
+    for (int q = 0; q < PS; ++q) two_sum_acc(ts, tc, sh.red[q * GM + tid]);
+    a.partial[((size_t)chunk * a.T + j_begin) * M + tid] = ts + tc;
   }
 }
 
@@ -1073,7 +1367,9 @@ __device__ __forceinline__ void update_group_combine(const UpdateArgs& a, int g,
     }
     __syncwarp(G == 32 ? 0xffffffffu : ((1u << G) - 1u));
     // every read of the group's old rows is done before any write below
-    if (idx < TM) {
+    if (idx < TM && a.export_out) {
+      a.export_out[2 + idx] = ns + nc;  // the combined N, not divided by Z
+    } else if (idx < TM) {
       if (a.shift) {
         if (tid >= M) a.U[idx - M] = v;
         else if (g == 0) {
@@ -1111,11 +1407,13 @@ __device__ __forceinline__ void update_final_body(const UpdateArgs& a, bool ok, 
     float zs = 0.0f, zc = 0.0f;
     for (int ch = tid; ch < a.chunks; ch += NT) two_sum_acc(zs, zc, __ldcg(a.zpart + ch));
     Z = block_sum2<NT>(zs, zc, sh.sh_s, sh.sh_c);
-    if (a.shift)
+    if (a.shift && !a.export_out)
       for (int q = tid; q < (a.groups - 1) * M; q += NT) {
         const int g = 1 + q / M, i = q % M;
         a.U[(size_t)(g * a.rows - 1) * M + i] = __ldcg(a.edge + g * M + i);
       }
+  } else if (a.export_out) {
+    for (int idx = tid; idx < a.T * M; idx += NT) a.export_out[2 + idx] = 0.0f;
   } else if (a.shift && a.u0_out && tid < M) {
     a.u0_out[tid] = __ldcg(a.U + tid);
   }
@@ -1125,8 +1423,13 @@ __device__ __forceinline__ void update_final_body(const UpdateArgs& a, bool ok, 
       a.diag[0] = rf;
       a.diag[1] = Z;
       a.diag[2] = rf * a.inv_lam - logf(Z / (float)a.K);
-    } else {
-      *a.status = kStatusNonFinite;
+      a.diag[3] = rho;
+    } else if (!a.export_out) {
+      *a.status = kStatusNonFinite;  // an exported shard may have no finite cost
+    }
+    if (a.export_out) {
+      a.export_out[0] = ok ? rho : INFINITY;
+      a.export_out[1] = ok ? Z : 0.0f;
     }
     *a.it = *a.it + a.it_advance;
     *a.rho_key = kKeyEmpty;
@@ -1140,9 +1443,18 @@ __device__ __forceinline__ void update_final_body(const UpdateArgs& a, bool ok, 
 // tickets are re-armed by their last holders.  An intermediate iteration of
 // an MPC step (no shift, no counter advance, every cost finite) needs no
 // final body: its diagnostics are overwritten by the next iteration.
-template <bool BF16, int M, int VPT>
+// SRC = 0: the partial body streams the stored perturbations (chunks of
+// rollouts); SRC = 1: it rescales and sums partial records (chunks of
+// records).
+template <bool BF16, int M, int VPT, int SRC>
 __global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateArgs a) {
-  __shared__ UpdateShared<kUpdateThreads, chunk_rollouts<BF16, M, VPT, kUpdateThreads>()> sh;
+  constexpr int kECap = chunk_rollouts<BF16, M, VPT, kUpdateThreads>();
+  __shared__ UpdateShared<kUpdateThreads, kECap> sh;
+  MJ_CHECK(blockDim.x == kUpdateThreads && (int)gridDim.x == a.chunks && (int)gridDim.y == a.groups &&
+               a.rows == kUpdateThreads / 32 && a.rows * M <= 32 && a.Kpad % 32 == 0 &&
+               (SRC == 0 ? (int)blockIdx.x * kUpdateThreads * VPT < a.Kpad * M / (BF16 ? 8 : 4)
+                         : (a.bps <= kECap && (int)blockIdx.x * a.bps < a.nb)),
+           a.status);
   griddep_launch_dependents();
   const int g = blockIdx.y;
   const int j_begin = g * a.rows;
@@ -1158,15 +1470,48 @@ __global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateA
   // only after this kernel has completed
   if (a.rho_key_next && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     *a.rho_key_next = kKeyEmpty;
-  UpdatePrefetch<BF16, M, VPT, kUpdateThreads> pf;
-  update_prefetch_noise<BF16, M, VPT, kUpdateThreads>(a, blockIdx.x, j_begin, j_end, pf);
-  update_prefetch_costs<BF16, M, VPT, kUpdateThreads>(a, blockIdx.x, pf);
-  const uint32_t key = __ldcg(a.rho_key);
-  const bool ok = key < kKeyInf;  // at least one finite cost
-  const float rho = ok ? key_to_float(key) : 0.0f;
-  if (ok) {
-    update_partial_body<BF16, M, VPT, kUpdateThreads>(
-        a, rho, blockIdx.x, j_begin, j_end, g == 0, a.zpart + (size_t)g * a.chunks + blockIdx.x, pf, sh);
+  float rho;
+  bool ok;
+  if constexpr (SRC == 0) {
+    UpdatePrefetch<BF16, M, VPT, kUpdateThreads> pf;
+    update_prefetch_noise<BF16, M, VPT, kUpdateThreads>(a, blockIdx.x, j_begin, j_end, pf);
+    update_prefetch_costs<BF16, M, VPT, kUpdateThreads>(a, blockIdx.x, pf);
+    const uint32_t key = __ldcg(a.rho_key);
+    ok = key < kKeyInf;  // at least one finite cost
+    rho = ok ? key_to_float(key) : 0.0f;
+    if (ok) {
+      update_partial_body<BF16, M, VPT, kUpdateThreads>(
+          a, rho, blockIdx.x, j_begin, j_end, g == 0, a.zpart + (size_t)g * a.chunks + blockIdx.x, pf, sh);
+    }
+  } else {
+    if (a.rho_from_rec) {
+      float r = INFINITY;
+      const size_t R = 2 + (size_t)a.T * M;
+      for (int b = threadIdx.x; b < a.nb; b += kUpdateThreads) r = fminf(r, __ldcg(a.rec + (size_t)b * R));
+      r = fminf(r, __shfl_xor_sync(0xffffffffu, r, 16));
+      r = fminf(r, __shfl_xor_sync(0xffffffffu, r, 8));
+      r = fminf(r, __shfl_xor_sync(0xffffffffu, r, 4));
+      r = fminf(r, __shfl_xor_sync(0xffffffffu, r, 2));
+      r = fminf(r, __shfl_xor_sync(0xffffffffu, r, 1));
+      if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = r;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float m = INFINITY;
+        for (int w = 0; w < kUpdateThreads / 32; ++w) m = fminf(m, sh.red[w]);
+        sh.rho = m;
+      }
+      __syncthreads();
+      rho = sh.rho;
+      ok = rho < INFINITY;
+    } else {
+      const uint32_t key = __ldcg(a.rho_key);
+      ok = key < kKeyInf;
+      rho = ok ? key_to_float(key) : 0.0f;
+    }
+    if (ok) {
+      update_partial_records<M, kUpdateThreads>(a, rho, blockIdx.x, j_begin, j_end,
+                                                a.zpart + (size_t)g * a.chunks + blockIdx.x, sh);
+    }
   }
   // the barrier orders the block's stores before thread 0's fence and
   // ticket; each winner fences again before reading what the others wrote
@@ -1196,11 +1541,12 @@ __global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateA
   if (threadIdx.x == 0) *a.done = 0u;
 }
 
-// w_k = e_k / Z for the weights getter.
-static __global__ void normalize_weights_kernel(const float* __restrict__ e, const float* __restrict__ diag,
-                                         int K, float* __restrict__ w) {
+// w_k = exp((rho - S~_k)/lambda) / Z for the weights getter (the e_k of the
+// update, normalised), from the costs and the diagnostics (Z, raw rho).
+static __global__ void weights_kernel(const float* __restrict__ s_part, const float* __restrict__ diag,
+                                      float inv_lam, int K, float* __restrict__ w) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < K) w[k] = e[k] / diag[1];
+  if (k < K) w[k] = expf((diag[3] - s_part[k]) * inv_lam) / diag[1];
 }
 
 }  // namespace mj

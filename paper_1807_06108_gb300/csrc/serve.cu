@@ -89,6 +89,7 @@ namespace {
 
 // Make session i resident within the budget; false if it must wait.
 bool make_resident(mppi_server* S, int i, int* status) {
+  mj::NvtxRange nv("mppi serve make resident");
   Session& ses = S->sessions[i];
   if (ses.ctx) return true;
   while (S->used + ses.bytes > S->budget) {
@@ -127,6 +128,7 @@ bool make_resident(mppi_server* S, int i, int* status) {
 
 // Launch ticket t of session i on slot s.
 mppi_status launch(mppi_server* S, Slot& slot, int i, uint64_t t) {
+  mj::NvtxRange nv("mppi serve admit");
   Session& ses = S->sessions[i];
   Request& r = S->reqs[t];
   mppi_jump_ctx* ctx = ses.ctx;

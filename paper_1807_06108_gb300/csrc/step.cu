@@ -19,7 +19,30 @@ using namespace mj;
 
 namespace {
 
+// The status word of a finished step as a return code, with its message.
+mppi_status status_of(mppi_jump_ctx* ctx, int st) {
+  if (st == MPPI_ENONFINITE)
+    snprintf(ctx->err, sizeof(ctx->err), "every rollout cost was non-finite; U left unchanged");
+  else if (st == MPPI_ETIMEOUT)
+    snprintf(ctx->err, sizeof(ctx->err), "a bounded device wait expired");
+  else if (st == MPPI_EBOUNDS)
+    snprintf(ctx->err, sizeof(ctx->err), "a kernel's launch check failed (checked build)");
+  return (mppi_status)st;
+}
+
+// The update's partial source for the context's tile: the records of the
+// rollout blocks (tile 4) or the stored perturbations.
+UpdateSource block_records(const mppi_jump_ctx* ctx) {
+  UpdateSource src = {nullptr, 0, 0, nullptr};
+  if (ctx->tile.variant == 4) {
+    src.rec = ctx->rec;
+    src.nb = (ctx->P.Kpad + ctx->tile.block - 1) / ctx->tile.block;
+  }
+  return src;
+}
+
 mppi_status capture_step(mppi_jump_ctx* ctx, int iters, cudaGraphExec_t* exec) {
+  NvtxRange nv("mppi step capture");
   const bool split = ctx->tile.variant >= 2;
   const size_t need_links = 2 * (size_t)iters + 2;
   while (ctx->links.size() < need_links) {
@@ -68,15 +91,16 @@ mppi_status capture_step(mppi_jump_ctx* ctx, int iters, cudaGraphExec_t* exec) {
       mark(3 * r);
       // the noise arrives through an event (an ordinary dependency); the
       // kernel before it in this stream is the previous update
-      if (e == cudaSuccess) e = launch_rollout_seq(ctx->P, b, ctx->tile, true, main);
+      if (e == cudaSuccess) e = launch_rollout_seq(ctx->P, b, ctx->tile, (uint32_t)r, true, main);
     } else {
       mark(3 * r);
       if (e == cudaSuccess) e = launch_rollout(ctx->P, b, ctx->tile, (uint32_t)r, false, main);
     }
     mark(3 * r + 1);
+    const UpdateSource src = block_records(ctx);
     if (e == cudaSuccess)
       e = launch_update(ctx->P, b, ctx->geom, r, last ? 1 : 0, last ? (uint32_t)iters : 0u,
-                        last ? ctx->u0 : nullptr, main);
+                        last ? ctx->u0 : nullptr, main, &src);
     mark(3 * r + 2);
     if (split && e == cudaSuccess) e = cudaEventRecord(evU[r], main);
   }
@@ -110,6 +134,7 @@ mppi_status get_graph(mppi_jump_ctx* ctx, int iters, cudaGraphExec_t* exec) {
 extern "C" {
 
 mppi_status mppi_jump_rollout_cost(mppi_jump_ctx* ctx, const float* x0, float* costs) {
+  NvtxRange nv("mppi rollout_cost (A1-A2)");
   if (!ctx || !x0) return MPPI_EINVAL;
   CK(cudaMemcpyAsync(ctx->x0, x0, sizeof(float) * ctx->P.n, cudaMemcpyDefault, ctx->stream), "x0 copy");
   const IterBuffers b = ctx_buffers(ctx, costs, 0);
@@ -120,9 +145,47 @@ mppi_status mppi_jump_rollout_cost(mppi_jump_ctx* ctx, const float* x0, float* c
 }
 
 mppi_status mppi_jump_update(mppi_jump_ctx* ctx) {
+  NvtxRange nv("mppi update (A3-A4)");
   if (!ctx) return MPPI_EINVAL;
-  CK(launch_update(ctx->P, ctx_buffers(ctx, nullptr, 0), ctx->geom, 0, 0, 1u, nullptr, ctx->stream),
+  const UpdateSource src = block_records(ctx);
+  CK(launch_update(ctx->P, ctx_buffers(ctx, nullptr, 0), ctx->geom, 0, 0, 1u, nullptr, ctx->stream, &src),
      "update launch");
+  return MPPI_OK;
+}
+
+mppi_status mppi_jump_set_rollout_offset(mppi_jump_ctx* ctx, uint32_t k_offset) {
+  if (!ctx) return MPPI_EINVAL;
+  if ((uint64_t)k_offset + (uint64_t)ctx->P.Kpad > 0x100000000ull)
+    return fail(ctx->err, MPPI_EINVAL, "rollout offset %u + K exceeds the 32-bit rollout index", k_offset);
+  CK(cudaStreamSynchronize(ctx->stream), "set_rollout_offset");
+  ctx->P.k_base = k_offset;
+  drop_graphs(ctx);
+  return MPPI_OK;
+}
+
+mppi_status mppi_jump_rollout_partial(mppi_jump_ctx* ctx, const float* x0, float* partial) {
+  NvtxRange nv("mppi rollout_partial");
+  if (!ctx || !x0 || !partial) return MPPI_EINVAL;
+  CK(cudaMemcpyAsync(ctx->x0, x0, sizeof(float) * ctx->P.n, cudaMemcpyDefault, ctx->stream), "x0 copy");
+  const IterBuffers b = ctx_buffers(ctx, nullptr, 0);
+  CK(launch_rollout(ctx->P, b, ctx->tile, 0u, true, ctx->stream), "rollout launch");
+  ctx->last_set = 0;
+  UpdateSource src = block_records(ctx);
+  src.export_out = partial;
+  CK(launch_update(ctx->P, b, ctx->geom, 0, 0, 0u, nullptr, ctx->stream, &src), "partial launch");
+  return MPPI_OK;
+}
+
+mppi_status mppi_jump_apply_partials(mppi_jump_ctx* ctx, const float* partials, int32_t n_parts, int32_t r,
+                                     int32_t shift, float* u0) {
+  NvtxRange nv("mppi apply_partials");
+  if (!ctx || !partials || n_parts < 1 || r < 0) return MPPI_EINVAL;
+  if (n_parts > records_per_chunk(ctx->P.m) * ctx->max_chunks)
+    return fail(ctx->err, MPPI_EINVAL, "%d partial records exceed the limit", n_parts);
+  const UpdateSource src = {partials, n_parts, 1, nullptr};
+  CK(launch_update(ctx->P, ctx_buffers(ctx, nullptr, 0), ctx->geom, r, shift ? 1 : 0, 1u, shift ? u0 : nullptr,
+                   ctx->stream, &src),
+     "apply launch");
   return MPPI_OK;
 }
 
@@ -132,11 +195,7 @@ mppi_status mppi_jump_sync(mppi_jump_ctx* ctx) {
      "status copy");
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status reset");
   CK(cudaStreamSynchronize(ctx->stream), "sync");
-  if (ctx->h_status[0] != 0) {
-    snprintf(ctx->err, sizeof(ctx->err), "every rollout cost was non-finite; U left unchanged");
-    return (mppi_status)ctx->h_status[0];
-  }
-  return MPPI_OK;
+  return status_of(ctx, ctx->h_status[0]);
 }
 
 mppi_status mppi_jump_set_tuning(mppi_jump_ctx* ctx, const mppi_jump_tuning* tuning_host) {
@@ -189,6 +248,7 @@ mppi_status mppi_jump_phase_times(mppi_jump_ctx* ctx, float out_host[2], int32_t
 }
 
 mppi_status mppi_jump_step_async(mppi_jump_ctx* ctx, const float* x0, int32_t iters, float* u0) {
+  NvtxRange nv("mppi step_async (graph replay)");
   if (!ctx || !x0 || iters < 1) return MPPI_EINVAL;
   cudaGraphExec_t ex;
   mppi_status st = get_graph(ctx, iters, &ex);
@@ -203,6 +263,7 @@ mppi_status mppi_jump_step_async(mppi_jump_ctx* ctx, const float* x0, int32_t it
 }
 
 mppi_status mppi_jump_step(mppi_jump_ctx* ctx, const float* x0_host, int32_t iters, float* u0_host) {
+  NvtxRange nv("mppi step (graph replay, host x0/u0)");
   if (!ctx || !x0_host || !u0_host || iters < 1) return MPPI_EINVAL;
   cudaGraphExec_t ex;
   mppi_status st = get_graph(ctx, iters, &ex);
@@ -219,15 +280,12 @@ mppi_status mppi_jump_step(mppi_jump_ctx* ctx, const float* x0_host, int32_t ite
      "status copy");
   CK(cudaStreamSynchronize(ctx->stream), "step sync");
   std::memcpy(u0_host, ctx->h_u0, sizeof(float) * ctx->P.m);
-  if (ctx->h_status[0] != 0) {
-    snprintf(ctx->err, sizeof(ctx->err), "every rollout cost was non-finite; U left unchanged");
-    return (mppi_status)ctx->h_status[0];
-  }
-  return MPPI_OK;
+  return status_of(ctx, ctx->h_status[0]);
 }
 
 mppi_status mppi_jump_autotune(mppi_jump_ctx* ctx, const float* x0, int32_t iters, int32_t reps,
                                mppi_jump_tuning* best_host, float* best_ms_host) {
+  NvtxRange nv("mppi autotune");
   if (!ctx || !x0 || iters < 1 || reps < 1) return MPPI_EINVAL;
   const size_t TM = (size_t)ctx->P.T * ctx->P.m;
   std::vector<float> U_save(TM);
@@ -248,6 +306,7 @@ mppi_status mppi_jump_autotune(mppi_jump_ctx* ctx, const float* x0, int32_t iter
   const RolloutTile cands[] = {{2, 128, 4}, {2, 64, 4},  {2, 32, 4},  {2, 128, 2}, {2, 64, 2},
                                {2, 32, 2},  {2, 128, 8}, {2, 64, 8},  {2, 32, 8},  {3, 128, 4},
                                {3, 128, 8}, {3, 64, 8},  {3, 32, 8},  {3, 128, 16}, {3, 64, 16},
+                               {4, 128, 8}, {4, 64, 8},  {4, 128, 16}, {4, 64, 16},
                                {1, 128, 4}, {1, 64, 4},  {1, 32, 4}};
   RolloutTile best = ctx->tile;
   float best_ms = 1e30f;

@@ -1,25 +1,24 @@
 """Multi-process helpers (one process per GPU).
 
-The MPC path shards by problem: every rank solves its own independent
-problems (a rank-specific Philox key), so nothing is exchanged in the data
-path and the job scales weakly; the only collective is the timing
-reduction (barrier, then the maximum of the ranks' elapsed times).
+Two ways to use several GPUs:
 
-For a single problem split over ranks by rollouts, the update of Eq. 37
-needs one exchange: each rank reduces its rollouts k in [k0, k1) to the
-partial (rho_g = min S~_k, Z_g = sum exp(-(S~_k - rho_g)/lambda),
-N_g = sum exp(-(S~_k - rho_g)/lambda) delta_k); with rho = min_g rho_g the
-global sums are Z = sum_g Z_g exp(-(rho_g - rho)/lambda) and likewise N, and
-dU = N / Z -- the same shift-invariant log-sum-exp rescaling the update
-kernel applies across its chunks.  `combine_partials` and
-`allreduce_partials` implement that exchange (T*m + 2 floats per rank).
+* independent problems: every rank solves its own problems (a rank-specific
+  Philox key), so nothing is exchanged in the data path and the job scales
+  weakly; the only collective is the timing reduction (barrier, then the
+  maximum of the ranks' elapsed times);
+* one problem split by rollouts: each rank is a shard context (its
+  configuration's K is the shard's rollout count, its rollout offset the
+  shard's first rollout, see shard_range) whose mppi_jump_rollout_partial
+  writes a partial record (rho_g, Z_g, N_g[T][m]) on the device;
+  allgather_records exchanges the records (an all-gather of T*m + 2 floats
+  per rank), and every rank applies all of them, in rank order, with
+  mppi_jump_apply_partials -- the combination (Eq. 37 over all rollouts)
+  runs in the library's kernel, so the ranks keep identical controls.
+
+This module moves data only; all arithmetic of the method is in the library.
 """
 
 from __future__ import annotations
-
-import math
-
-import numpy as np
 
 
 def rank_seed(seed, rank):
@@ -35,46 +34,14 @@ def shard_range(K, rank, world):
     return k0, k0 + base + (1 if rank < extra else 0)
 
 
-def partial_from_costs(S, delta, lam):
-    """(rho_g, Z_g, N_g) of one shard: S [k], delta [T][k][m] (float64)."""
-    S = np.asarray(S, dtype=np.float64)
-    finite = np.isfinite(S)
-    if not finite.any():
-        return math.inf, 0.0, np.zeros(delta.shape[0::2])
-    rho = float(S[finite].min())
-    e = np.where(finite, np.exp(-(np.where(finite, S, rho) - rho) / lam), 0.0)
-    N = np.einsum("k,tkm->tm", e, np.asarray(delta, dtype=np.float64))
-    return rho, float(e.sum()), N
-
-
-def combine_partials(parts, lam):
-    """dU = sum_g N_g w_g / sum_g Z_g w_g with w_g = exp(-(rho_g - rho)/lam)."""
-    rho = min(p[0] for p in parts)
-    if not math.isfinite(rho):
-        raise ValueError("every rollout cost is non-finite")
-    Z = 0.0
-    N = None
-    for r, z, n in parts:
-        w = math.exp(-(r - rho) / lam) if math.isfinite(r) else 0.0
-        Z += z * w
-        N = n * w if N is None else N + n * w
-    return N / Z, rho, Z
-
-
-def allreduce_partials(dist, rho_g, Z_g, N_g, lam):
-    """The exchange across ranks of a torch.distributed group (any backend):
-    one MIN all-reduce of rho_g and one SUM all-reduce of the rescaled
-    (Z_g, N_g).  Returns (dU, rho, Z) on every rank."""
+def allgather_records(dist, record):
+    """All-gather of one partial record per rank (a 1-D float32 tensor of
+    2 + T*m values, on the device for NCCL, on the host for gloo); returns a
+    [world][2 + T*m] tensor in rank order on the same device."""
     import torch
-    t = torch.tensor([rho_g], dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MIN)
-    rho = float(t.item())
-    w = math.exp(-(rho_g - rho) / lam) if math.isfinite(rho_g) else 0.0
-    buf = torch.cat([torch.tensor([Z_g * w], dtype=torch.float64),
-                     torch.as_tensor(np.asarray(N_g, dtype=np.float64) * w).reshape(-1)])
-    dist.all_reduce(buf, op=dist.ReduceOp.SUM)
-    Z = float(buf[0].item())
-    return (buf[1:].numpy().reshape(np.asarray(N_g).shape) / Z), rho, Z
+    parts = [torch.empty_like(record) for _ in range(dist.get_world_size())]
+    dist.all_gather(parts, record.contiguous())
+    return torch.stack(parts)
 
 
 def max_over_ranks(dist, value, device="cpu"):

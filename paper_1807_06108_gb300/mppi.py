@@ -22,7 +22,9 @@ import numpy as np
 from . import build as _build
 from . import workloads as _wl
 
-LIB_PATH = _build.LIB
+# MPPI_JUMP_LIB selects another build of the library, e.g. the checked debug
+# variant (_build.LIB_CHECKED).
+LIB_PATH = os.environ.get("MPPI_JUMP_LIB") or _build.LIB
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -33,8 +35,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 MAX_JUMPS = 16
 STATUS = {0: "MPPI_OK", 1: "MPPI_EINVAL", 2: "MPPI_ENOMEM", 3: "MPPI_ECUDA",
-          4: "MPPI_ETIMEOUT", 5: "MPPI_ENONFINITE", 6: "MPPI_EBUSY"}
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EBUSY = range(7)
+          4: "MPPI_ETIMEOUT", 5: "MPPI_ENONFINITE", 6: "MPPI_EBUSY", 7: "MPPI_EBOUNDS"}
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EBUSY, EBOUNDS = range(8)
 
 
 class MppiError(RuntimeError):
@@ -77,8 +79,8 @@ class Config(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    """mppi_jump_tuning: rollout variant (1 fused, 2 split), threads per block
-    and steps per unrolled chunk."""
+    """mppi_jump_tuning: rollout variant (1 fused, 2 split, 3 staged, 4 staged
+    with block records), threads per block and steps per chunk or stage."""
     _fields_ = [("rollout_variant", ctypes.c_int32), ("rollout_block", ctypes.c_int32),
                 ("rollout_chunk", ctypes.c_int32)]
 
@@ -128,6 +130,9 @@ _sig("mppi_jump_get_noise", _st, _CTX, _vp)
 _sig("mppi_jump_get_weights", _st, _CTX, _vp)
 _sig("mppi_jump_get_free_energy", _st, _CTX, _P(ctypes.c_float))
 _sig("mppi_jump_get_state", _st, _CTX, _vp, _P(ctypes.c_size_t))
+_sig("mppi_jump_set_rollout_offset", _st, _CTX, ctypes.c_uint32)
+_sig("mppi_jump_rollout_partial", _st, _CTX, _vp, _vp)
+_sig("mppi_jump_apply_partials", _st, _CTX, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp)
 _sig("mppi_jump_set_state", _st, _CTX, _vp, ctypes.c_size_t)
 
 
@@ -207,6 +212,19 @@ def mppi_jump_rollout_cost(ctx, x0_ptr, costs_ptr=0):
 
 def mppi_jump_update(ctx):
     _check(_lib.mppi_jump_update(ctx), "update", ctx)
+
+
+def mppi_jump_set_rollout_offset(ctx, k_offset):
+    _check(_lib.mppi_jump_set_rollout_offset(ctx, int(k_offset)), "set_rollout_offset", ctx)
+
+
+def mppi_jump_rollout_partial(ctx, x0_ptr, partial_ptr):
+    _check(_lib.mppi_jump_rollout_partial(ctx, _vp(x0_ptr), _vp(partial_ptr)), "rollout_partial", ctx)
+
+
+def mppi_jump_apply_partials(ctx, partials_ptr, n_parts, r=0, shift=0, u0_ptr=0):
+    _check(_lib.mppi_jump_apply_partials(ctx, _vp(partials_ptr), int(n_parts), int(r), int(shift),
+                                         _vp(u0_ptr or None)), "apply_partials", ctx)
 
 
 def mppi_jump_step(ctx, x0_host, iters, u0_host):
@@ -457,6 +475,26 @@ class Solver:
     def free_energy(self):
         return mppi_jump_get_free_energy(self.ctx)
 
+    # -- rollout shards ---------------------------------------------------
+    def set_rollout_offset(self, k0):
+        mppi_jump_set_rollout_offset(self.ctx, k0)
+
+    def rollout_partial(self, x0):
+        """This shard's partial record (rho, Z, N[T][m]) as a device tensor."""
+        self.set_x0(x0)
+        with self._on():
+            out = self.torch.empty(2 + self.T * self.m, dtype=self.torch.float32, device=self.device)
+            mppi_jump_rollout_partial(self.ctx, self.x0.data_ptr(), out.data_ptr())
+        return out
+
+    def apply_partials(self, parts, r=0, shift=False):
+        """Combine partial records [G][2 + T*m] (device tensor) into U."""
+        with self._on():
+            p = parts.to(self.device, dtype=self.torch.float32).contiguous()
+            mppi_jump_apply_partials(self.ctx, p.data_ptr(), p.shape[0], r, int(bool(shift)),
+                                     self.u0.data_ptr() if shift else 0)
+        self._sync()
+
     def get_state(self):
         return mppi_jump_get_state(self.ctx)
 
@@ -479,6 +517,8 @@ _sig("mppi_batch_set_controls", _st, _vp, ctypes.c_int32, _vp)
 _sig("mppi_batch_get_iteration", _st, _vp, ctypes.c_int32, _P(ctypes.c_uint32))
 _sig("mppi_batch_set_tuning", _st, _vp, ctypes.c_int32)
 _sig("mppi_batch_get_tuning", _st, _vp, _P(ctypes.c_int32))
+_sig("mppi_batch_set_tile", _st, _vp, ctypes.c_int32, ctypes.c_int32)
+_sig("mppi_batch_get_tile", _st, _vp, _P(ctypes.c_int32), _P(ctypes.c_int32))
 _sig("mppi_batch_autotune", _st, _vp, _vp, ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_float))
 _sig("mppi_batch_info", _st, _vp, _P(ctypes.c_int64), _P(ctypes.c_int32), _P(ctypes.c_int32))
 _sig("mppi_batch_inject_stall", _st, _vp, ctypes.c_int32)
@@ -583,11 +623,21 @@ class Batch:
         _bcheck(_lib.mppi_batch_get_tuning(self.handle, ctypes.byref(v)), "batch_get_tuning", self.handle)
         return v.value
 
+    def set_tile(self, block, chunk):
+        _bcheck(_lib.mppi_batch_set_tile(self.handle, int(block), int(chunk)), "batch_set_tile", self.handle)
+
+    def tile(self):
+        b, c = ctypes.c_int32(0), ctypes.c_int32(0)
+        _bcheck(_lib.mppi_batch_get_tile(self.handle, ctypes.byref(b), ctypes.byref(c)), "batch_get_tile",
+                self.handle)
+        return b.value, c.value
+
     def autotune(self, reps=3):
+        """Returns ((block, chunk), mean batched-step ms) of the fastest tile."""
         blk, ms = ctypes.c_int32(0), ctypes.c_float(0.0)
         _bcheck(_lib.mppi_batch_autotune(self.handle, _vp(self.x0s.data_ptr()), int(reps),
                                          ctypes.byref(blk), ctypes.byref(ms)), "batch_autotune", self.handle)
-        return blk.value, ms.value
+        return self.tile(), ms.value
 
     def inject_stall(self, on=True):
         _bcheck(_lib.mppi_batch_inject_stall(self.handle, int(bool(on))), "batch_inject_stall",

@@ -50,18 +50,28 @@ def test_rollout_tiles_are_bit_identical(cuda, prob):
     rng = np.random.default_rng(0)
     x0, U = W.random_state(prob, rng, 0.1), W.random_controls(prob, rng, 0.2)
     ref = _one_iteration(prob, x0, U, 3, (1, 128, 4))
-    for tile in [(2, 128, 4), (2, 64, 2), (2, 32, 8), (1, 32, 4), (2, 96, 4), (3, 128, 8),
-                 (3, 64, 4), (3, 32, 16), (3, 96, 8)]:
+    for tile in [(2, 128, 4), (2, 64, 2), (2, 32, 8), (1, 32, 4), (1, 64, 8), (1, 128, 16), (2, 96, 4),
+                 (3, 128, 8), (3, 64, 4), (3, 32, 16), (3, 96, 8)]:
         got = _one_iteration(prob, x0, U, 3, tile)
         for a, b in zip(ref, got):
             np.testing.assert_array_equal(a, b)
+    # block records (tile 4): the same costs, perturbations, counts and marks;
+    # the update sums in another order
+    U0 = U.astype(np.float64)
+    for tile in [(4, 128, 8), (4, 64, 4), (4, 32, 16)]:
+        got = _one_iteration(prob, x0, U, 3, tile)
+        for i in (0, 2, 3, 4):
+            np.testing.assert_array_equal(ref[i], got[i])
+        dU_ref, dU = ref[1] - U0, got[1] - U0
+        assert np.max(np.abs(dU - dU_ref)) <= 1e-5 * np.max(np.abs(dU_ref))
+        np.testing.assert_allclose(got[5], ref[5], rtol=1e-5, atol=1e-12)
 
 
 def test_invalid_tile_rejected(cuda):
     from paper_1807_06108_gb300 import mppi
     s = _solver(W.cartpole_k1000(K=64, T=4))
     try:
-        for bad in [(0, 128, 4), (4, 128, 4), (3, 128, 2), (2, 128, 16), (2, 48, 4), (2, 256, 4),
+        for bad in [(0, 128, 4), (5, 128, 4), (4, 128, 2), (1, 128, 2), (3, 128, 2), (2, 128, 16), (2, 48, 4), (2, 256, 4),
                     (1, 16, 4), (2, 64, 3)]:
             with pytest.raises(mppi.MppiError):
                 mppi.mppi_jump_set_tuning(s.ctx, *bad)
@@ -70,15 +80,16 @@ def test_invalid_tile_rejected(cuda):
         s.close()
 
 
+@pytest.mark.parametrize("tile", [None, (4, 128, 8)], ids=["default_tile", "block_records"])
 @pytest.mark.parametrize("prob", [W.cartpole_k1000(), W.quadrotor_k4096(K=1024, T=60, iters=4),
                                   W.large_quadrotor()],
                          ids=["cartpole_K1000_T50", "quadrotor_K1024_T60_it4",
                               "quadrotor_K65536_T200_it5_bf16_streaming_update"])
-def test_graph_step_equals_direct_calls_and_oracle(cuda, prob):
+def test_graph_step_equals_direct_calls_and_oracle(cuda, prob, tile):
     x0 = W.initial_state(prob)
     iters = prob["iters"]
     # graph-replayed step through the synchronous host call
-    s = _solver(prob)
+    s = _solver(prob, tile)
     try:
         u0 = s.step(x0)
         U_step = s.controls()
@@ -86,7 +97,7 @@ def test_graph_step_equals_direct_calls_and_oracle(cuda, prob):
     finally:
         s.close()
     # the same iterations through rollout_cost / update, then the shift by hand
-    s = _solver(prob)
+    s = _solver(prob, tile)
     try:
         for _ in range(iters):
             s.rollout_cost(x0, want_costs=False)

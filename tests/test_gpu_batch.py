@@ -69,30 +69,33 @@ def test_block_sizes_agree_and_autotune_restores(cuda):
     probs = _mixed("bf16")
     states = _states(probs, np.random.default_rng(1))
     results = {}
-    for block in (64, 128, 256):
+    for tile in [(64, 4), (128, 4), (256, 4), (128, 8), (64, 8)]:
         b = mppi.Batch(probs)
         try:
-            b.set_tuning(block)
-            assert b.tuning() == block
+            b.set_tile(*tile)
+            assert b.tile() == tile and b.tuning() == tile[0]
             b.step(states)
-            results[block] = [b.controls(i) for i in range(len(probs))]
+            results[tile] = [b.controls(i) for i in range(len(probs))]
         finally:
             b.close()
-    for block in (64, 256):
+    for tile in [(64, 4), (256, 4), (128, 8), (64, 8)]:
         for i in range(len(probs)):
-            ref = results[128][i].astype(np.float64)
+            ref = results[(128, 4)][i].astype(np.float64)
             den = max(np.max(np.abs(ref - W.initial_controls(probs[i]))), 1e-30)
-            assert np.max(np.abs(results[block][i] - ref)) / den <= 1e-4 * probs[i]["iters"]
+            assert np.max(np.abs(results[tile][i] - ref)) / den <= 1e-4 * probs[i]["iters"]
+    # the chunk only reorders when the random numbers are drawn: same block, same result
+    for i in range(len(probs)):
+        np.testing.assert_array_equal(results[(128, 8)][i], results[(128, 4)][i])
     b = mppi.Batch(probs)
     try:
         b.set_states(states)
-        blk, ms = b.autotune(reps=1)
-        assert blk in (64, 128, 256) and ms > 0
+        (blk, ch), ms = b.autotune(reps=1)
+        assert blk in (64, 128, 256) and ch in (4, 8) and ms > 0
         assert all(b.iteration(i) == 0 for i in range(len(probs)))
-        b.set_tuning(128)
+        b.set_tile(128, 4)
         b.step(states)
         for i in range(len(probs)):
-            np.testing.assert_array_equal(b.controls(i), results[128][i])
+            np.testing.assert_array_equal(b.controls(i), results[(128, 4)][i])
     finally:
         b.close()
 

@@ -94,8 +94,9 @@ def test_iteration_matches_oracle(cuda, name):
     _record(name, rep)
 
 
-@pytest.mark.parametrize("tile", [(1, 64, 4), (2, 96, 8), (3, 32, 4)],
-                         ids=["fused", "split", "staged_small_blocks"])
+@pytest.mark.parametrize("tile", [(1, 64, 4), (2, 96, 8), (3, 32, 4), (4, 128, 8), (4, 32, 16)],
+                         ids=["fused", "split", "staged_small_blocks", "block_records",
+                              "block_records_small_blocks"])
 def test_other_rollout_tiles_match_oracle(cuda, tile):
     """Non-default launch shapes against the oracle directly (they are also
     compared bit for bit with one another in test_gpu_api)."""
@@ -104,8 +105,9 @@ def test_other_rollout_tiles_match_oracle(cuda, tile):
     _record(f"quadrotor_laplace_bf16_sqrtdt_tile{tile}", rep)
 
 
-@pytest.mark.parametrize("tile", [(1, 64, 4), (2, 96, 8), (3, 32, 4), (3, 128, 16)],
-                         ids=["fused", "split", "staged_small_blocks", "staged_long_stages"])
+@pytest.mark.parametrize("tile", [(1, 64, 4), (2, 96, 8), (3, 32, 4), (3, 128, 16), (4, 96, 8)],
+                         ids=["fused", "split", "staged_small_blocks", "staged_long_stages",
+                              "block_records"])
 @pytest.mark.parametrize("name", ["cartpole_rows02_f32", "cartpole_rows02_bf16",
                                   "quadrotor_rows012_f32", "quadrotor_rows012_bf16"])
 def test_non_default_jump_rows_every_tile_matches_oracle(cuda, name, tile):
@@ -115,16 +117,17 @@ def test_non_default_jump_rows_every_tile_matches_oracle(cuda, name, tile):
     _record(f"{name}_tile{tile}", rep)
 
 
-def test_large_quadrotor_sampled_and_full_update(cuda):
+@pytest.mark.parametrize("tile", [None, (4, 128, 8)], ids=["default", "block_records"])
+def test_large_quadrotor_sampled_and_full_update(cuda, tile):
     """K=65536, T=200, dt=0.005, Laplace marks at 5/s, bfloat16 noise: every
     rollout's counts, marks, noise and cost, and the full update, against the
     oracle over all K."""
     prob = W.large_quadrotor()
     x0, U = W.initial_state(prob), W.initial_controls(prob)
-    g = parity.gpu_iteration(prob, x0, U, 0)
+    g = parity.gpu_iteration(prob, x0, U, 0, tile=tile)
     r = parity.oracle_iteration(prob, x0, U, 0)
     rep = parity.compare_iteration(prob, U, g, r)
-    _record("quadrotor_K65536_T200_bf16_laplace", rep)
+    _record(f"quadrotor_K65536_T200_bf16_laplace_tile{tile}", rep)
 
 
 def test_maximum_rollout_count(cuda):

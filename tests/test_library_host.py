@@ -120,3 +120,15 @@ def test_workspace_bytes_scale_with_problem(lib):
     assert small >= 4096 * 100 * 4 * 4
     assert big >= 65536 * 200 * 4 * 2
     assert big > small
+
+
+def test_checked_debug_build_exports_the_same_symbols(lib):
+    """The MPPI_CHECK_BOUNDS variant (launch checks that report MPPI_EBOUNDS
+    through the status word) builds and exports every declared entry point."""
+    path = B.build(checked=True)
+    assert path == B.LIB_CHECKED and os.path.exists(path)
+    so = ctypes.CDLL(path)
+    missing = [n for n in _declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+    so.mppi_jump_status_string.restype = ctypes.c_char_p
+    assert so.mppi_jump_status_string(7) == b"kernel launch check failed"
