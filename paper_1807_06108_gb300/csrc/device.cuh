@@ -66,16 +66,48 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
   return make_uint4(c0, c1, c2, c3);
 }
 
-// Uniform on (0, 1): (top 23 bits + 1/2) * 2^-23, exact in float32.
+// Uniform on (0, 1): (top 23 bits + 1/2) * 2^-23, exact in float32 (one
+// fused multiply-add of exact terms).
 __device__ __forceinline__ float uniform01(uint32_t w) {
-  return (__uint2float_rn(w >> 9) + 0.5f) * 0x1p-23f;
+  return fmaf(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
+}
+
+// sin(2 pi u) and cos(2 pi u) for the uniforms above.  8u is exact; its
+// integer part q (0..7) is the octant and its fraction f (exact) places the
+// angle (pi/4) g within it, g = f (even octants) or 1 - f (odd octants,
+// exact), so that sin and cos of (pi/4) g, g in [0, 1], cover every octant
+// through the symmetries sin(pi/2 - a) = cos a, sin(pi + a) = -sin a.  They
+// come from their Taylor series in g, to degree 9 and 10 (truncation below
+// 3e-9); the coefficients are (pi/4)^n / n! with alternating signs.  Over all
+// 2^23 uniforms the float32 result is within 1.1 ulp of sin and cos (checked
+// against a double-precision evaluation).
+__device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
+  constexpr float kS1 = 0.785398163397448f, kS3 = -0.0807455121882808f, kS5 = 0.00249039457019272f,
+                  kS7 = -3.65762041821772e-05f, kS9 = 3.13361689037812e-07f;
+  constexpr float kC2 = -0.308425137534042f, kC4 = 0.0158543442438155f, kC6 = -0.00032599188692739f,
+                  kC8 = 3.59086044859151e-06f, kC10 = -2.4611369504942e-08f;
+  const float x = 8.0f * u;
+  const float xq = floorf(x);
+  const int q = (int)xq;
+  const float f = x - xq;
+  const float g = (q & 1) ? 1.0f - f : f;
+  const float g2 = g * g;
+  const float sp = g * fmaf(g2, fmaf(g2, fmaf(g2, fmaf(g2, kS9, kS7), kS5), kS3), kS1);
+  const float cp = fmaf(g2, fmaf(g2, fmaf(g2, fmaf(g2, fmaf(g2, kC10, kC8), kC6), kC4), kC2), 1.0f);
+  const bool swap = ((q + 1) & 2) != 0;  // octants 1, 2, 5, 6
+  const float sv = swap ? cp : sp, cv = swap ? sp : cp;
+  s = q >= 4 ? -sv : sv;
+  c = (q >= 2 && q <= 5) ? -cv : cv;
 }
 
 // Box-Muller (1958): r = sqrt(-2 ln u_a), (r cos 2 pi u_b, r sin 2 pi u_b).
+// -2 ln u_a >= 1.2e-7 for these uniforms (u_a <= 1 - 2^-24), so the square
+// root is taken as x * rsqrt(x) (within 3 ulp).
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, float& z1) {
-  const float r = sqrtf(-2.0f * logf(uniform01(wa)));
+  const float x = -2.0f * logf(uniform01(wa));
+  const float r = x * rsqrtf(x);
   float s, c;
-  sincospif(2.0f * uniform01(wb), &s, &c);
+  sincos_2pi(uniform01(wb), s, c);
   z0 = r * c;
   z1 = r * s;
 }

@@ -279,22 +279,35 @@ bool valid_tile(const RolloutTile& t) {
   return t.variant == 2 && (t.chunk == 2 || t.chunk == 4 || t.chunk == 8);
 }
 
+// Where the marks of state-channel jumps are drawn.  While the rollout blocks
+// fit on the SMs at once (the rollout is latency-bound and the noise pass
+// runs beside it on the other SMs), the noise pass draws them in its own
+// threads and writes the records, one launch fewer before the first rollout
+// of a step (measured on GB300 at K = 4096: 0.2393 ms per MPC step against
+// 0.2527 ms with marks_kernel).  Beyond that the per-thread mark loop, run by
+// a warp as often as its busiest lane has jumps, is a fifth of an issue-bound
+// pass, and marks_kernel draws them with the warp's lanes on jumps instead.
+static bool marks_in_noise(const DevProblem& P) {
+  return P.jump_channel == MPPI_JUMP_STATE && (P.Kpad + kRolloutThreads - 1) / kRolloutThreads <= num_sms_of_current();
+}
+
 template <int M, bool BF16, bool DBG, bool MARKS>
 static void launch_noise_t(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s) {
   const dim3 grid((P.Kpad + kNoiseThreads - 1) / kNoiseThreads, (P.T + 3) / 4);
   float4* jrec = P.jump_channel == MPPI_JUMP_STATE ? b.jrec : nullptr;
-  noise_kernel<M, BF16, DBG, MARKS><<<grid, kNoiseThreads, 0, s>>>(P, b.it, it_off, b.noise, b.counts, jrec,
-                                                                   b.dbg_counts, b.dbg_J, b.status);
+  noise_kernel<M, BF16, DBG, MARKS><<<grid, kNoiseThreads, 0, s>>>(
+      P, b.it, it_off, b.noise, b.counts, jrec, marks_in_noise(P) ? 1 : 0, b.dbg_counts, b.dbg_J, b.status);
 }
 
 template <int M, bool BF16>
 static void launch_noise_m(const DevProblem& P, const IterBuffers& b, uint32_t it_off, bool dbg,
                            cudaStream_t s) {
   // the marks are drawn here for control-channel jumps (folded into
-  // delta_eff) and for the debug copy of J; state-channel jumps are drawn by
-  // the rollout
+  // delta_eff), for the debug copy of J and for state-channel records of
+  // small problems
   if (dbg) launch_noise_t<M, BF16, true, true>(P, b, it_off, s);
-  else if (P.jump_channel == MPPI_JUMP_CONTROL) launch_noise_t<M, BF16, false, true>(P, b, it_off, s);
+  else if (P.jump_channel == MPPI_JUMP_CONTROL || marks_in_noise(P))
+    launch_noise_t<M, BF16, false, true>(P, b, it_off, s);
   else launch_noise_t<M, BF16, false, false>(P, b, it_off, s);
 }
 
@@ -306,8 +319,8 @@ cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_
     case 2: launch_noise_m<4, false>(P, b, it_off, dbg, s); break;
     default: launch_noise_m<4, true>(P, b, it_off, dbg, s); break;
   }
-  // state-channel jumps: their marks into the jump records
-  if (P.jump_channel == MPPI_JUMP_STATE && P.nmax > 0) {
+  // state-channel jumps of large problems: their marks into the jump records
+  if (P.jump_channel == MPPI_JUMP_STATE && P.nmax > 0 && !marks_in_noise(P)) {
     const int per_block = kMarkSpan * (kMarkThreads / 32);
     const dim3 grid((P.Kpad + per_block - 1) / per_block, P.T);
     marks_kernel<<<grid, kMarkThreads, 0, s>>>(P, b.it, it_off, b.counts, b.jrec, b.status);

@@ -362,20 +362,20 @@ __device__ __forceinline__ void fused_rollout_thread(
 // rounding applied) and the jump counts counts[j*Kpad + k]; consecutive
 // threads take consecutive k, so every store is contiguous.  MARKS: the
 // thread also draws the marks of its jumps -- for control-channel jumps,
-// which are folded into delta_eff, and for the debug copy of J.  For
-// state-channel jumps the marks are drawn by marks_kernel from the counts
-// (only a few percent of the steps jump) into the jump records, which stay
-// zero except where the count is positive: this pass resets the record of
-// any step that jumped when the buffer set was last written and does not
-// jump now.  The pass touches nothing the rollout or update of another
-// iteration reads, so it can run concurrently with them on a second buffer
-// set.
+// which are folded into delta_eff, for the debug copy of J, and (with
+// jrec_marks) for the jump records of state-channel jumps.  Otherwise the
+// records are written by marks_kernel from the counts.  The records stay zero
+// except where the count is positive: this pass resets the record of any step
+// that jumped when the buffer set was last written and does not jump now.  The
+// pass touches nothing the rollout or update of another iteration reads, so
+// it can run concurrently with them on a second buffer set.
 // ---------------------------------------------------------------------------
 template <int M, bool BF16, bool DBG, bool MARKS>
 __global__ void __launch_bounds__(kNoiseThreads)
 noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t it_off,
              void* __restrict__ noise, uint8_t* __restrict__ counts, float4* __restrict__ jrec,
-             uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J, int* __restrict__ status) {
+             int jrec_marks, uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J,
+             int* __restrict__ status) {
   static_assert(MARKS || !DBG, "the debug copy of J needs the marks");
   MJ_CHECK(blockDim.x == kNoiseThreads && 4 * (int)blockIdx.y < P.T && P.Kpad % 32 == 0 && P.K <= P.Kpad &&
                P.m == M,
@@ -439,7 +439,10 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
     }
     store_noise<M, BF16>(noise, row, de, active);  // rounds to bfloat16 (RNE) when BF16
     const uint8_t cnew = active ? (uint8_t)N[jj] : (uint8_t)0;
-    if (jrec && cnew == 0 && counts[row] != 0) jrec[row] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (jrec) {
+      if (MARKS && jrec_marks && cnew != 0) jrec[row] = make_float4(J[jj][0], J[jj][1], J[jj][2], J[jj][3]);
+      else if (cnew == 0 && counts[row] != 0) jrec[row] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
     counts[row] = cnew;
     if (DBG && active) {
       const size_t rk = (size_t)j * P.K + k;
@@ -478,11 +481,14 @@ marks_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
   // Kpad is a multiple of 32, so kt < Kpad keeps all 16 bytes in the row
   if (kt < P.Kpad) x = *reinterpret_cast<const uint4*>(counts + (size_t)j * P.Kpad + kt);
   const uint32_t wd[4] = {x.x, x.y, x.z, x.w};
-  uint32_t nz = 0u;
+  // bit 7 of each byte of nzw[q] is set when that count byte is nonzero
+  uint32_t nzw[4];
+  int ne = 0;  // 0 .. 16
 #pragma unroll
-  for (int q = 0; q < 16; ++q)
-    if ((wd[q >> 2] >> (8 * (q & 3))) & 0xffu) nz |= 1u << q;
-  const int ne = __popc(nz);  // 0 .. 16
+  for (int q = 0; q < 4; ++q) {
+    nzw[q] = (((wd[q] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | wd[q]) & 0x80808080u;
+    ne += __popc(nzw[q]);
+  }
   uint32_t bal[5];
 #pragma unroll
   for (int b = 0; b < 5; ++b) bal[b] = __ballot_sync(0xffffffffu, (ne >> b) & 1);
@@ -495,8 +501,14 @@ marks_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
   }
   if (total == 0) return;  // the same for every lane of the warp
 #pragma unroll
-  for (int q = 0; q < 16; ++q)
-    if ((nz >> q) & 1u) list[w][pos++] = ((uint32_t)(16 * lane + q) << 5) | ((wd[q >> 2] >> (8 * (q & 3))) & 0xffu);
+  for (int q = 0; q < 4; ++q) {
+    uint32_t m = nzw[q];
+    while (m) {  // this lane's jumping steps, in rollout order
+      const int byte = (__ffs(m) - 1) >> 3;
+      list[w][pos++] = ((uint32_t)(16 * lane + 4 * q + byte) << 5) | ((wd[q] >> (8 * byte)) & 0xffu);
+      m &= m - 1u;
+    }
+  }
   __syncwarp();
   const uint32_t it = __ldg(it_ptr) + it_off;
   for (int e = lane; e < total; e += 32) {
@@ -697,7 +709,7 @@ __host__ __device__ constexpr uint32_t staged_smem_total(int nt, int m, int sb, 
 // (update_kernel with the record source), with no second pass over the
 // perturbations.
 template <int SYS, bool BF16, int S, int JM, bool PART>
-__global__ void __launch_bounds__(kStagedMaxThreads, 4)
+__global__ void __launch_bounds__(kStagedMaxThreads, PART ? 4 : 0)
 rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
                       const void* __restrict__ noise, const float4* __restrict__ jrec,
                       float* __restrict__ s_part, uint32_t* __restrict__ rho_key, int* __restrict__ status,
@@ -1036,9 +1048,12 @@ costs_kernel(const float* __restrict__ U, int T, float lam, float4 inv_sigma2,
 // dU = sum_c N_c / Z, U += alpha dU; it then emits u0 and shifts the sequence
 // when asked, writes the free-energy diagnostics, advances the iteration
 // counter and re-arms the running minimum.  This is Eq. 37 with the
-// normalisation applied once at the end; every sum is compensated and every
-// order fixed, so the result does not depend on scheduling.  Data that other
-// blocks of the same launch wrote is read through L2 (ld.global.cg).
+// normalisation applied once at the end.  Each lane accumulates its share of
+// a row (up to 64 products at K = 65536) in plain float32 fused
+// multiply-adds; the lanes' sums, the chunk partials, Z and the group sums
+// are merged with compensated (TwoSum) additions.  Every order is fixed, so
+// the result does not depend on scheduling.  Data that other blocks of the
+// same launch wrote is read through L2 (ld.global.cg).
 // ---------------------------------------------------------------------------
 struct UpdateArgs {
   const void* noise;
