@@ -59,13 +59,14 @@ SUB_WORKLOADS = {"quadrotor_k4096": (200, 5.0), "cartpole_k1000": (400, 3.0)}
 METRIC = "trajectory-steps/s (MPC solves of MPPI on jump diffusions)"
 
 # Source-level lane operations per trajectory step (each 32-bit integer or
-# float32 add / mul / fma / xor / compare / select counts 1; the accurate log
-# 8, sqrt 4, sincospi 20; the hardware __sincosf 3 and __fdividef 2), counted
-# from the kernel source: SEQ = cost + plant + Euler step of the sequential
-# rollout kernel, NOISE = Philox, Box-Muller, perturbation and jump count of
-# the sampling kernel.  The fused tile does both in one kernel.
+# float32 add / mul / fma / xor / compare / select counts 1, a 32x32->64
+# multiply 2; logf 8, rsqrtf 4, the octant sin/cos of 2 pi u 24; the hardware
+# __sincosf 3 and __fdividef 2), counted from the kernel source: SEQ = cost +
+# plant + Euler step of the sequential rollout kernel, NOISE = Philox,
+# Box-Muller, perturbation and jump count of the sampling kernel.  The fused
+# tile does both in one kernel.
 SEQ_OPS_PER_STEP = {"cartpole": 64.0, "quadrotor": 154.0}
-NOISE_OPS_PER_STEP = {"cartpole": 79.0, "quadrotor": 218.0}
+NOISE_OPS_PER_STEP = {"cartpole": 80.0, "quadrotor": 230.0}
 L2_BYTES = 129 * 1024 * 1024
 
 VARIANT_NAMES = {1: "fused", 2: "split", 3: "staged", 4: "staged_block_records"}

@@ -229,11 +229,16 @@ struct Plant<1> {
     xd[3] = a * (cph * sth * cps + sph * sps);
     xd[4] = a * (cph * sth * sps - sph * cps);
     xd[5] = a * (cph * cth) - p.qg;
+    // phi' = p + (sin phi q + cos phi r) tan theta, psi' = (sin phi q +
+    // cos phi r) / cos theta: the common factor is formed while the
+    // reciprocal of cos theta is computed, leaving two dependent operations
+    // after it on the step's longest dependency chain
     const float inv_cth = __fdividef(1.0f, cth);
-    const float tth = sth * inv_cth;
-    xd[6] = wp + sph * tth * wq + cph * tth * wr;
+    const float a_qr = fmaf(sph, wq, cph * wr);
+    const float b_qr = a_qr * inv_cth;
+    xd[6] = fmaf(b_qr, sth, wp);
     xd[7] = cph * wq - sph * wr;
-    xd[8] = (sph * wq + cph * wr) * inv_cth;
+    xd[8] = b_qr;
     const float taux = p.arm * (v[1] - v[3]);
     const float tauy = p.arm * (v[2] - v[0]);
     const float tauz = p.kappa * (v[0] - v[1] + v[2] - v[3]);

@@ -283,8 +283,9 @@ bool valid_tile(const RolloutTile& t) {
 // fit on the SMs at once (the rollout is latency-bound and the noise pass
 // runs beside it on the other SMs), the noise pass draws them in its own
 // threads and writes the records, one launch fewer before the first rollout
-// of a step (measured on GB300 at K = 4096: 0.2393 ms per MPC step against
-// 0.2527 ms with marks_kernel).  Beyond that the per-thread mark loop, run by
+// of a step (measured on GB300: cart-pole K = 1000, T = 50 at 0.0360 ms per
+// MPC step against 0.0409 ms with marks_kernel; quadrotor K = 4096, T = 100
+// unchanged at 0.251 ms).  Beyond that the per-thread mark loop, run by
 // a warp as often as its busiest lane has jumps, is a fifth of an issue-bound
 // pass, and marks_kernel draws them with the warp's lanes on jumps instead.
 static bool marks_in_noise(const DevProblem& P) {

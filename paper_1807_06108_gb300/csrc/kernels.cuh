@@ -363,12 +363,13 @@ __device__ __forceinline__ void fused_rollout_thread(
 // threads take consecutive k, so every store is contiguous.  MARKS: the
 // thread also draws the marks of its jumps -- for control-channel jumps,
 // which are folded into delta_eff, for the debug copy of J, and (with
-// jrec_marks) for the jump records of state-channel jumps.  Otherwise the
-// records are written by marks_kernel from the counts.  The records stay zero
-// except where the count is positive: this pass resets the record of any step
-// that jumped when the buffer set was last written and does not jump now.  The
-// pass touches nothing the rollout or update of another iteration reads, so
-// it can run concurrently with them on a second buffer set.
+// jrec_marks) for the jump records of state-channel jumps, all of which it
+// then writes (J, zero without a jump).  Otherwise the records are written by
+// marks_kernel from the counts and stay zero except where the count is
+// positive: this pass resets the record of any step that jumped when the
+// buffer set was last written and does not jump now.  The pass touches
+// nothing the rollout or update of another iteration reads, so it can run
+// concurrently with them on a second buffer set.
 // ---------------------------------------------------------------------------
 template <int M, bool BF16, bool DBG, bool MARKS>
 __global__ void __launch_bounds__(kNoiseThreads)
@@ -440,8 +441,13 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
     store_noise<M, BF16>(noise, row, de, active);  // rounds to bfloat16 (RNE) when BF16
     const uint8_t cnew = active ? (uint8_t)N[jj] : (uint8_t)0;
     if (jrec) {
-      if (MARKS && jrec_marks && cnew != 0) jrec[row] = make_float4(J[jj][0], J[jj][1], J[jj][2], J[jj][3]);
-      else if (cnew == 0 && counts[row] != 0) jrec[row] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      // drawing the marks here (small problems): every record, J or zero, with
+      // no read of the previous count; otherwise only the stale records
+      if (MARKS && jrec_marks)
+        jrec[row] = active ? make_float4(J[jj][0], J[jj][1], J[jj][2], J[jj][3])
+                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      else if (cnew == 0 && counts[row] != 0)
+        jrec[row] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     counts[row] = cnew;
     if (DBG && active) {
@@ -458,15 +464,16 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
 // ---------------------------------------------------------------------------
 // Split form, part 1b (state-channel jumps).  marks_kernel: the marks of every
 // step whose count is positive, with the lanes of a warp busy on jumps
-// rather than on steps.  A warp covers 512 consecutive rollouts of one step j
-// (a 16-byte load of counts per lane), lists the jumping steps in shared
+// rather than on steps.  A warp covers 1024 consecutive rollouts of one step
+// j (two 16-byte loads of counts per lane), lists the jumping steps in shared
 // memory (a ballot prefix sum: deterministic positions) and draws each one's
 // summed marks on one lane (draw_marks, streams 2+n, as every other form
-// does), writing J into the step's jump record.  Grid (ceil(Kpad / 2048), T),
-// kMarkThreads threads.
+// does), writing J into the step's jump record.  At the large workload's jump
+// probability (2.5 % per step) a warp lists about 26 steps: one pass of its
+// lanes.  Grid (ceil(Kpad / 4096), T), kMarkThreads threads.
 // ---------------------------------------------------------------------------
 constexpr int kMarkThreads = 128;
-constexpr int kMarkSpan = 512;  // rollouts per warp
+constexpr int kMarkSpan = 1024;  // rollouts per warp
 
 static __global__ void __launch_bounds__(kMarkThreads)
 marks_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t it_off,
@@ -476,36 +483,40 @@ marks_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
   const int j = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int kw = (blockIdx.x * (kMarkThreads / 32) + w) * kMarkSpan;  // the warp's first rollout
-  const int kt = kw + 16 * lane;
-  uint4 x = make_uint4(0u, 0u, 0u, 0u);
-  // Kpad is a multiple of 32, so kt < Kpad keeps all 16 bytes in the row
-  if (kt < P.Kpad) x = *reinterpret_cast<const uint4*>(counts + (size_t)j * P.Kpad + kt);
-  const uint32_t wd[4] = {x.x, x.y, x.z, x.w};
+  const int kt = kw + 32 * lane;
+  uint32_t wd[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  // Kpad is a multiple of 32, so kt < Kpad keeps all 32 bytes in the row
+  if (kt < P.Kpad) {
+    const uint4* src = reinterpret_cast<const uint4*>(counts + (size_t)j * P.Kpad + kt);
+    const uint4 a = src[0], b = src[1];
+    wd[0] = a.x; wd[1] = a.y; wd[2] = a.z; wd[3] = a.w;
+    wd[4] = b.x; wd[5] = b.y; wd[6] = b.z; wd[7] = b.w;
+  }
   // bit 7 of each byte of nzw[q] is set when that count byte is nonzero
-  uint32_t nzw[4];
-  int ne = 0;  // 0 .. 16
+  uint32_t nzw[8];
+  int ne = 0;  // 0 .. 32
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < 8; ++q) {
     nzw[q] = (((wd[q] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | wd[q]) & 0x80808080u;
     ne += __popc(nzw[q]);
   }
-  uint32_t bal[5];
+  uint32_t bal[6];
 #pragma unroll
-  for (int b = 0; b < 5; ++b) bal[b] = __ballot_sync(0xffffffffu, (ne >> b) & 1);
+  for (int b = 0; b < 6; ++b) bal[b] = __ballot_sync(0xffffffffu, (ne >> b) & 1);
   const uint32_t lt = (1u << lane) - 1u;
   int total = 0, pos = 0;
 #pragma unroll
-  for (int b = 0; b < 5; ++b) {
+  for (int b = 0; b < 6; ++b) {
     total += __popc(bal[b]) << b;
     pos += __popc(bal[b] & lt) << b;
   }
   if (total == 0) return;  // the same for every lane of the warp
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < 8; ++q) {
     uint32_t m = nzw[q];
     while (m) {  // this lane's jumping steps, in rollout order
       const int byte = (__ffs(m) - 1) >> 3;
-      list[w][pos++] = ((uint32_t)(16 * lane + 4 * q + byte) << 5) | ((wd[q] >> (8 * byte)) & 0xffu);
+      list[w][pos++] = ((uint32_t)(32 * lane + 4 * q + byte) << 5) | ((wd[q] >> (8 * byte)) & 0xffu);
       m &= m - 1u;
     }
   }
@@ -767,6 +778,7 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
 
   if (tid >= nt) {
     // ---- producer warp: lane 0 issues every stage's copies
+    if (!PART && tid != nt) return;
     if (tid == nt) {
       const uint32_t j_bytes = kJ ? (uint32_t)nk * 16u : 0u;
       for (int st = 0; st < n_stages && ok; ++st) {
@@ -797,6 +809,12 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
         atomicExch(status, kStatusTimeout);
         if (PART) *abort_flag = 1;
       }
+      if (!PART) {
+        // leave only when the copies of the last two stages have landed (bounded)
+        for (int ls = max(0, issued - 2); ls < issued; ++ls)
+          mbar_wait_bounded(landed + (ls & 1), (uint32_t)(ls >> 1) & 1u, kCopyWaitNs);
+        return;
+      }
     }
     issued = __shfl_sync(0xffffffffu, issued, 0);
   } else {
@@ -812,6 +830,7 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
       const int buf = st & 1;
       if (!mbar_wait_bounded(landed + buf, (uint32_t)(st >> 1) & 1u, kCopyWaitNs)) {
         atomicExch(status, kStatusTimeout);
+        if (!PART) return;
         ok = false;
         break;
       }
@@ -857,11 +876,13 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
       __syncwarp();
       if ((tid & 31) == 0) mbar_arrive(empty + buf);
     }
-    if (!PART && !ok) return;
     griddep_wait();  // the running minimum was re-armed by the previous update
-    float sk = INFINITY;
-    if (mine && ok) sk = finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
-    if (PART) {
+    if constexpr (!PART) {
+      if (mine) finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
+      return;
+    } else {
+      float sk = INFINITY;
+      if (mine && ok) sk = finish_rollout<SYS>(P, k, active, x, s, sc, s_part, rho_key);
       tail[tid] = sk;
       if (!ok) *abort_flag = 1;
     }
@@ -960,7 +981,7 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
       }
     }
   }
-  if (tid == nt) {
+  if (PART && tid == nt) {
     // leave only when the copies of the last two issued stages have landed (bounded)
     for (int ls = max(0, issued - 2); ls < issued; ++ls)
       mbar_wait_bounded(landed + (ls & 1), (uint32_t)(ls >> 1) & 1u, kCopyWaitNs);
@@ -973,13 +994,13 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
 
 // Shared scratch of the update bodies for NT threads: per-warp partial sums
 // and the weights of one chunk of rollouts (ECAP floats).
-template <int NT, int ECAP>
+template <int NT, int ECAP, bool REC = false>
 struct UpdateShared {
   float sh_s[NT / 32], sh_c[NT / 32];
   unsigned ticket;
   float rho;
   __align__(16) float e[ECAP];
-  float red[NT];
+  float red[REC ? NT : 1];  // partial sums of the record source
 };
 
 // Rollouts per chunk of the weighted sum: NT * VPT 16-byte vectors of a row.
@@ -1464,7 +1485,7 @@ __device__ __forceinline__ void update_final_body(const UpdateArgs& a, bool ok, 
 template <bool BF16, int M, int VPT, int SRC>
 __global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateArgs a) {
   constexpr int kECap = chunk_rollouts<BF16, M, VPT, kUpdateThreads>();
-  __shared__ UpdateShared<kUpdateThreads, kECap> sh;
+  __shared__ UpdateShared<kUpdateThreads, kECap, SRC == 1> sh;
   MJ_CHECK(blockDim.x == kUpdateThreads && (int)gridDim.x == a.chunks && (int)gridDim.y == a.groups &&
                a.rows == kUpdateThreads / 32 && a.rows * M <= 32 && a.Kpad % 32 == 0 &&
                (SRC == 0 ? (int)blockIdx.x * kUpdateThreads * VPT < a.Kpad * M / (BF16 ? 8 : 4)
