@@ -28,7 +28,7 @@ IterBuffers ctx_buffers(mppi_jump_ctx* ctx, float* costs, int set) {
   b.x0 = ctx->x0;
   b.U = ctx->U;
   b.noise = ctx->noise[set];
-  b.counts = ctx->counts[set];
+  b.jmask = ctx->jmask[set];
   b.jrec = ctx->jrec[set];
   b.s_part = ctx->s_part;
   b.rec = ctx->rec;
@@ -59,7 +59,7 @@ void drop_graphs(mppi_jump_ctx* ctx) {
 namespace {
 
 struct Layout {
-  size_t x0, U, noise[2], counts[2], jrec[2], s_part, rec, partial, zpart, gpart, scal, status, it,
+  size_t x0, U, noise[2], jmask[2], jrec[2], s_part, rec, partial, zpart, gpart, scal, status, it,
       rho_key, done, u0, total;
   int max_chunks;
 };
@@ -81,8 +81,9 @@ Layout layout_of(const DevProblem& P, const UpdateGeom& g) {
   L.U = take(sizeof(float) * (size_t)P.T * P.m);
   for (int s = 0; s < 2; ++s) {
     L.noise[s] = take(sb * TK * P.m);
-    L.counts[s] = take(TK);
-    L.jrec[s] = take(P.jump_channel == MPPI_JUMP_STATE ? sizeof(float4) * TK : 0);
+    const bool sj = P.jump_channel == MPPI_JUMP_STATE;
+    L.jmask[s] = take(sj ? sizeof(uint32_t) * (size_t)(P.Kpad / 32) * mask_cols(P.T) : 0);
+    L.jrec[s] = take(sj ? sizeof(float4) * TK : 0);
   }
   L.s_part = take(sizeof(float) * P.Kpad);
   // partial records of the rollout blocks (tile 4; the smallest block is 32)
@@ -255,8 +256,9 @@ mppi_status mppi_jump_init(const mppi_jump_config* cfg, void* stream, mppi_jump_
       ctx->U = (float*)(a + L.U);
       for (int s = 0; s < 2; ++s) {
         ctx->noise[s] = a + L.noise[s];
-        ctx->counts[s] = (uint8_t*)(a + L.counts[s]);
-        ctx->jrec[s] = ctx->P.jump_channel == MPPI_JUMP_STATE ? (float4*)(a + L.jrec[s]) : nullptr;
+        const bool sj = ctx->P.jump_channel == MPPI_JUMP_STATE;
+        ctx->jmask[s] = sj ? (uint32_t*)(a + L.jmask[s]) : nullptr;
+        ctx->jrec[s] = sj ? (float4*)(a + L.jrec[s]) : nullptr;
       }
       ctx->s_part = (float*)(a + L.s_part);
       ctx->rec = (float*)(a + L.rec);

@@ -23,7 +23,7 @@ struct mppi_jump_ctx {
   float* x0 = nullptr;          // [n]
   float* U = nullptr;           // [T][m]
   void* noise[2] = {};          // two sets of [T][Kpad][m] delta_eff (f32 or bf16)
-  uint8_t* counts[2] = {};      // [T][Kpad] jump counts
+  uint32_t* jmask[2] = {};      // [Kpad/32][mask_cols(T)] jump masks (state jumps)
   float4* jrec[2] = {};         // [T][Kpad] jump records (state jumps)
   float* s_part = nullptr;      // [Kpad]
   float* rec = nullptr;         // [ceil(Kpad/32)][2 + T*m] partial records of the rollout blocks

@@ -40,6 +40,11 @@ struct DevProblem {
   DevPlant pl;
 };
 
+// Columns of a jump-mask row (one row per 32 rollouts, one 32-bit word per
+// step): the steps rounded up to 16, so that every row starts on a 64-byte
+// boundary and the words of steps 4b .. 4b+3 are one aligned 16-byte store.
+__host__ __device__ constexpr int mask_cols(int T) { return (T + 15) & ~15; }
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds, each two
 // 32x32->64-bit products whose high halves are xored with the other two

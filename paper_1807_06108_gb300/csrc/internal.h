@@ -77,8 +77,10 @@ struct IterBuffers {
   const float* x0;
   float* U;
   void* noise;         // [T][Kpad][m] delta_eff, float32 or bfloat16
-  uint8_t* counts;     // [T][Kpad] jump counts
-  float4* jrec;        // [T][Kpad] jump records J (state jumps; zero without a jump)
+  uint32_t* jmask;     // [Kpad/32][mask_cols(T)] jump masks (sparse records): bit l of
+                       // word [w][j] set when rollout 32w+l jumps at step j
+  float4* jrec;        // [T][Kpad] jump records J (state jumps; dense: every step, zero
+                       // without a jump; sparse: valid where the mask bit is set)
   float* s_part;       // [Kpad] k-dependent cost part
   float* partial;      // [chunks][T][m] (max_chunks chunks)
   int max_chunks;      // chunks the partial and zpart buffers hold
@@ -99,6 +101,32 @@ struct IterBuffers {
 
 // Split variant, part 1: noise of iteration *it + it_off into b.noise etc.
 cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s);
+
+// State-channel jump records: dense (the noise pass draws the marks and
+// writes every step's record) while the rollout blocks of 128 fit on the SMs
+// at once, sparse beyond (jump masks, marks_kernel, gathered records).
+bool marks_in_noise(const DevProblem& P);
+// The jump masks of sparse records, or NULL (dense records, control-channel
+// jumps).
+uint32_t* sparse_mask(const DevProblem& P, const IterBuffers& b);
+
+// One launch of the staged rollout (staged.cu, staged_sparse.cu): the dense
+// and sparse jump-record forms are instantiated in two translation units.
+constexpr int kStagedSmemMax = 160 * 1024;
+struct StagedLaunch {
+  const DevProblem* P;
+  const IterBuffers* b;
+  const RolloutTile* tile;
+  int blocks;
+  size_t smem;
+  bool pdl;
+  cudaStream_t s;
+  bool part;
+};
+void launch_staged_dense(const StagedLaunch& L, int jump_mode);  // kJumpNone, kJumpDefault, kJumpRows
+void launch_staged_sparse(const StagedLaunch& L, bool velocity_rows);
+cudaError_t prepare_staged_dense();  // the kernels' shared-memory limits
+cudaError_t prepare_staged_sparse();
 // Split variant, part 2: the sequential rollout of iteration *it + it_off
 // over the stored noise.  pdl: launch as a programmatic dependent of the
 // previous kernel in the stream, which must then not be the noise pass that

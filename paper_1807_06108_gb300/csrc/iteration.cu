@@ -8,6 +8,7 @@
 
 #include "internal.h"
 #include "kernels.cuh"
+#include "launch.cuh"
 
 namespace mj {
 
@@ -148,50 +149,22 @@ mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg) 
 }
 
 // How the staged rollout applies the problem's state jumps (kJumpNone,
-// kJumpDefault or kJumpRows).
+// kJumpDefault or kJumpRows; the sparse forms are chosen at launch).
 static int jump_mode(const DevProblem& P) {
   if (P.jump_channel != MPPI_JUMP_STATE) return kJumpNone;
   return P.jump_default ? kJumpDefault : kJumpRows;
 }
 
 // Dynamic shared memory of the staged rollout: two stages of S steps of the
-// block's delta_eff rows, jump-mark table and counts (state jumps) and the S
-// control rows, the six mbarriers and the producer's jump list.
+// block's delta_eff rows, jump-record slots (state jumps) and control rows,
+// the four mbarriers and (block records) the record scratch.
 static size_t staged_smem_bytes(const DevProblem& P, int block, int S, bool part) {
   return staged_smem_total(block, P.m, P.noise_bf16 ? 2 : 4, S, jump_mode(P) != kJumpNone, part);
 }
 
-constexpr int kStagedSmemMax = 160 * 1024;
-
-template <int SYS, bool BF16, int JM, bool PART>
-static cudaError_t allow_staged_smem() {
-  cudaError_t e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 4, JM, PART>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 8, JM, PART>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(rollout_staged_kernel<SYS, BF16, 16, JM, PART>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
-  return e;
-}
-
-template <int SYS, bool BF16>
-static cudaError_t allow_staged_smem_all() {
-  cudaError_t e = allow_staged_smem<SYS, BF16, kJumpNone, false>();
-  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpDefault, false>();
-  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpRows, false>();
-  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpNone, true>();
-  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpDefault, true>();
-  if (e == cudaSuccess) e = allow_staged_smem<SYS, BF16, kJumpRows, true>();
-  return e;
-}
-
 cudaError_t prepare_kernels() {
-  cudaError_t e = allow_staged_smem_all<0, false>();
-  if (e == cudaSuccess) e = allow_staged_smem_all<0, true>();
-  if (e == cudaSuccess) e = allow_staged_smem_all<1, false>();
-  if (e == cudaSuccess) e = allow_staged_smem_all<1, true>();
+  cudaError_t e = prepare_staged_dense();
+  if (e == cudaSuccess) e = prepare_staged_sparse();
   return e;
 }
 
@@ -225,36 +198,8 @@ UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms) {
 // rollout launches as a programmatic dependent of the update before it,
 // which hides its launch latency and lets its copies of the step data start
 // early (it calls griddep_wait() before it touches anything the update
-// writes); the update launches as an ordinary dependent of the rollout.
-static int high_priority() {
-  static int prio = [] {
-    int least = 0, greatest = 0;
-    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
-    return greatest;
-  }();
-  return prio;
-}
-
-template <class... Params, class... Args>
-static void launch_hi(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                      bool pdl, Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[2];
-  attr[0].id = cudaLaunchAttributePriority;
-  attr[0].val.priority = high_priority();
-  // a programmatic dependent of the previous kernel in the stream: it may be
-  // scheduled once that kernel's blocks have all started, and waits in
-  // griddep_wait() for its completion before touching what it wrote
-  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[1].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 2 : 1;
-  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
+// writes); the update launches as an ordinary dependent of the rollout
+// (launch_hi, launch.cuh).
 
 // Measured on GB300: the staged form (a producer warp moves the step data
 // into shared memory with bulk copies) is the fastest rollout at every size;
@@ -279,25 +224,36 @@ bool valid_tile(const RolloutTile& t) {
   return t.variant == 2 && (t.chunk == 2 || t.chunk == 4 || t.chunk == 8);
 }
 
-// Where the marks of state-channel jumps are drawn.  While the rollout blocks
-// fit on the SMs at once (the rollout is latency-bound and the noise pass
-// runs beside it on the other SMs), the noise pass draws them in its own
-// threads and writes the records, one launch fewer before the first rollout
-// of a step (measured on GB300: cart-pole K = 1000, T = 50 at 0.0360 ms per
-// MPC step against 0.0409 ms with marks_kernel; quadrotor K = 4096, T = 100
-// unchanged at 0.251 ms).  Beyond that the per-thread mark loop, run by
-// a warp as often as its busiest lane has jumps, is a fifth of an issue-bound
-// pass, and marks_kernel draws them with the warp's lanes on jumps instead.
-static bool marks_in_noise(const DevProblem& P) {
+// Where the marks of state-channel jumps are drawn, and in which record form.
+// While the rollout blocks fit on the SMs at once (the rollout is
+// latency-bound and the noise pass runs beside it on the other SMs), the
+// noise pass draws them in its own threads and writes dense records (J or
+// zero for every step), which the rollout copies as whole rows: one launch
+// fewer before the first rollout of a step and no per-record copies in the
+// rollout's latency chain (measured on GB300: cart-pole K = 1000, T = 50 at
+// 0.0360 ms per MPC step against 0.0409 ms with marks_kernel).  Beyond that
+// the per-thread mark loop, run by a warp as often as its busiest lane has
+// jumps, is a fifth of an issue-bound pass; there the noise pass writes jump
+// masks, marks_kernel draws the marks with the warp's lanes on jumps and
+// writes sparse records, and the rollout gathers only those (the dense rows
+// would double the bytes it reads).
+bool marks_in_noise(const DevProblem& P) {
   return P.jump_channel == MPPI_JUMP_STATE && (P.Kpad + kRolloutThreads - 1) / kRolloutThreads <= num_sms_of_current();
+}
+
+// The jump masks of sparse records, or NULL (dense records, control-channel
+// jumps).
+uint32_t* sparse_mask(const DevProblem& P, const IterBuffers& b) {
+  return P.jump_channel == MPPI_JUMP_STATE && !marks_in_noise(P) ? b.jmask : nullptr;
 }
 
 template <int M, bool BF16, bool DBG, bool MARKS>
 static void launch_noise_t(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s) {
   const dim3 grid((P.Kpad + kNoiseThreads - 1) / kNoiseThreads, (P.T + 3) / 4);
-  float4* jrec = P.jump_channel == MPPI_JUMP_STATE ? b.jrec : nullptr;
+  const bool sj = P.jump_channel == MPPI_JUMP_STATE;
   noise_kernel<M, BF16, DBG, MARKS><<<grid, kNoiseThreads, 0, s>>>(
-      P, b.it, it_off, b.noise, b.counts, jrec, marks_in_noise(P) ? 1 : 0, b.dbg_counts, b.dbg_J, b.status);
+      P, b.it, it_off, b.noise, sparse_mask(P, b), sj ? b.jrec : nullptr, marks_in_noise(P) ? 1 : 0,
+      b.dbg_counts, b.dbg_J, b.status);
 }
 
 template <int M, bool BF16>
@@ -322,9 +278,9 @@ cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_
   }
   // state-channel jumps of large problems: their marks into the jump records
   if (P.jump_channel == MPPI_JUMP_STATE && P.nmax > 0 && !marks_in_noise(P)) {
-    const int per_block = kMarkSpan * (kMarkThreads / 32);
-    const dim3 grid((P.Kpad + per_block - 1) / per_block, P.T);
-    marks_kernel<<<grid, kMarkThreads, 0, s>>>(P, b.it, it_off, b.counts, b.jrec, b.status);
+    const int rows = P.Kpad / 32;
+    const dim3 grid((rows + kMarkWarps - 1) / kMarkWarps, (P.T + 31) / 32);
+    marks_kernel<<<grid, kMarkThreads, 0, s>>>(P, b.it, it_off, b.jmask, b.jrec, b.status);
   }
   return cudaGetLastError();
 }
@@ -335,42 +291,17 @@ static void launch_seq_t(const DevProblem& P, const IterBuffers& b, const Rollou
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
   if (tile.chunk == 2)
     launch_hi(rollout_split_kernel<SYS, BF16, 2>, dim3(blocks), dim3(tile.block), 0, s, pdl,
-        P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status);
+        P, b.x0, b.U, b.noise, sparse_mask(P, b), b.jrec, b.s_part, b.rho_key, b.status);
   else if (tile.chunk == 8)
     launch_hi(rollout_split_kernel<SYS, BF16, 8>, dim3(blocks), dim3(tile.block), 0, s, pdl,
-        P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status);
+        P, b.x0, b.U, b.noise, sparse_mask(P, b), b.jrec, b.s_part, b.rho_key, b.status);
   else
     launch_hi(rollout_split_kernel<SYS, BF16, 4>, dim3(blocks), dim3(tile.block), 0, s, pdl,
-        P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status);
+        P, b.x0, b.U, b.noise, sparse_mask(P, b), b.jrec, b.s_part, b.rho_key, b.status);
 }
 
-template <int SYS, bool BF16, int JM, bool PART>
-static void launch_staged_s(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile, int blocks,
-                            size_t smem, uint32_t it_off, bool pdl, cudaStream_t s) {
-  if (tile.chunk == 4)
-    launch_hi(rollout_staged_kernel<SYS, BF16, 4, JM, PART>, dim3(blocks), dim3(tile.block + 32), smem, s,
-        pdl, P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status, b.rec);
-  else if (tile.chunk == 16)
-    launch_hi(rollout_staged_kernel<SYS, BF16, 16, JM, PART>, dim3(blocks), dim3(tile.block + 32), smem, s,
-        pdl, P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status, b.rec);
-  else
-    launch_hi(rollout_staged_kernel<SYS, BF16, 8, JM, PART>, dim3(blocks), dim3(tile.block + 32), smem, s,
-        pdl, P, b.x0, b.U, b.noise, b.jrec, b.s_part, b.rho_key, b.status, b.rec);
-}
-
-template <int SYS, bool BF16, bool PART>
-static void launch_staged_j(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile, int blocks,
-                            size_t smem, uint32_t it_off, bool pdl, cudaStream_t s) {
-  const int jm = jump_mode(P);
-  if (jm == kJumpNone) launch_staged_s<SYS, BF16, kJumpNone, PART>(P, b, tile, blocks, smem, it_off, pdl, s);
-  else if (jm == kJumpDefault)
-    launch_staged_s<SYS, BF16, kJumpDefault, PART>(P, b, tile, blocks, smem, it_off, pdl, s);
-  else launch_staged_s<SYS, BF16, kJumpRows, PART>(P, b, tile, blocks, smem, it_off, pdl, s);
-}
-
-template <int SYS, bool BF16>
-static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile,
-                                   uint32_t it_off, bool pdl, cudaStream_t s) {
+static cudaError_t launch_staged(const DevProblem& P, const IterBuffers& b, const RolloutTile& tile, bool pdl,
+                                 cudaStream_t s) {
   const int blocks = (P.Kpad + tile.block - 1) / tile.block;
   const bool part = tile.variant == 4;
   if (part && !b.rec) return cudaErrorInvalidValue;
@@ -383,8 +314,10 @@ static cudaError_t launch_staged_t(const DevProblem& P, const IterBuffers& b, co
   // K = 4096 quadrotor with control-channel jumps took 0.427 ms against
   // 0.280 ms with the reservation (0.344 ms with 100 KB).
   if (blocks <= num_sms_of_current()) smem = (size_t)kStagedSmemMax;
-  if (part) launch_staged_j<SYS, BF16, true>(P, b, tile, blocks, smem, it_off, pdl, s);
-  else launch_staged_j<SYS, BF16, false>(P, b, tile, blocks, smem, it_off, pdl, s);
+  const StagedLaunch L = {&P, &b, &tile, blocks, smem, pdl, s, part};
+  const int jm = jump_mode(P);
+  if (jm != kJumpNone && sparse_mask(P, b)) launch_staged_sparse(L, jm == kJumpDefault);
+  else launch_staged_dense(L, jm);
   return cudaSuccess;
 }
 
@@ -392,13 +325,7 @@ cudaError_t launch_rollout_seq(const DevProblem& P, const IterBuffers& b, const 
                                uint32_t it_off, bool pdl, cudaStream_t s) {
   if (!valid_tile(tile) || tile.variant == 1) return cudaErrorInvalidValue;
   if (tile.variant >= 3) {
-    cudaError_t e = cudaSuccess;
-    switch (P.system * 2 + (P.noise_bf16 ? 1 : 0)) {
-      case 0: e = launch_staged_t<0, false>(P, b, tile, it_off, pdl, s); break;
-      case 1: e = launch_staged_t<0, true>(P, b, tile, it_off, pdl, s); break;
-      case 2: e = launch_staged_t<1, false>(P, b, tile, it_off, pdl, s); break;
-      default: e = launch_staged_t<1, true>(P, b, tile, it_off, pdl, s); break;
-    }
+    const cudaError_t e = launch_staged(P, b, tile, pdl, s);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }

@@ -359,22 +359,23 @@ __device__ __forceinline__ void fused_rollout_thread(
 // threadIdx.x and b = blockIdx.y, draws steps 4b .. 4b+3 of rollout k (the
 // four steps that share one jump-count Philox block), so the sampling runs
 // over K * T/4 threads instead of K.  It stores delta_eff (the bfloat16
-// rounding applied) and the jump counts counts[j*Kpad + k]; consecutive
-// threads take consecutive k, so every store is contiguous.  MARKS: the
-// thread also draws the marks of its jumps -- for control-channel jumps,
-// which are folded into delta_eff, for the debug copy of J, and (with
-// jrec_marks) for the jump records of state-channel jumps, all of which it
-// then writes (J, zero without a jump).  Otherwise the records are written by
-// marks_kernel from the counts and stay zero except where the count is
-// positive: this pass resets the record of any step that jumped when the
-// buffer set was last written and does not jump now.  The pass touches
-// nothing the rollout or update of another iteration reads, so it can run
-// concurrently with them on a second buffer set.
+// rounding applied); consecutive threads take consecutive k, so every store
+// is contiguous.  MARKS: the thread also draws the marks of its jumps -- for
+// control-channel jumps, which are folded into delta_eff, for the debug copy
+// of J, and (with jrec_marks) for dense state-channel jump records, which it
+// writes for every step (J, or zero without a jump).  Sparse state-channel
+// records (jmask != NULL): the pass stores the jump masks, a warp's ballot of
+// "count > 0" per step, bit l of jmask[w][j] for rollout 32w + l (padding
+// rollouts 0), lane 0 writing the four steps' words at once; marks_kernel
+// then writes the records where a bit is set, and a record is read only
+// there, so none is ever cleared.  The pass touches nothing the rollout or
+// update of another iteration reads, so it can run concurrently with them on
+// a second buffer set.
 // ---------------------------------------------------------------------------
 template <int M, bool BF16, bool DBG, bool MARKS>
 __global__ void __launch_bounds__(kNoiseThreads)
 noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t it_off,
-             void* __restrict__ noise, uint8_t* __restrict__ counts, float4* __restrict__ jrec,
+             void* __restrict__ noise, uint32_t* __restrict__ jmask, float4* __restrict__ jrec,
              int jrec_marks, uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J,
              int* __restrict__ status) {
   static_assert(MARKS || !DBG, "the debug copy of J needs the marks");
@@ -418,6 +419,16 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
           for (int c = 0; c < 4; ++c) J[q][c] = Jt[c];
     }
   }
+  if ((!MARKS || DBG) && jmask) {  // sparse records are drawn by marks_kernel
+    // the warp's 32 rollouts: one mask word per step (zero past T)
+    uint4 mw;
+    mw.x = __ballot_sync(0xffffffffu, active && N[0] > 0);
+    mw.y = __ballot_sync(0xffffffffu, active && N[1] > 0);
+    mw.z = __ballot_sync(0xffffffffu, active && N[2] > 0);
+    mw.w = __ballot_sync(0xffffffffu, active && N[3] > 0);
+    if ((threadIdx.x & 31) == 0)
+      reinterpret_cast<uint4*>(jmask + (size_t)(k >> 5) * mask_cols(P.T))[b] = mw;
+  }
   float zc[4];
   if constexpr (M == 1) normals4(philox4x32_10(uk, (uint32_t)b, it, 0u, P.key0, P.key1), zc);
 #pragma unroll
@@ -439,17 +450,8 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
       for (int i = 0; i < M; ++i) de[i] = __fadd_rn(de[i], J[jj][i]);
     }
     store_noise<M, BF16>(noise, row, de, active);  // rounds to bfloat16 (RNE) when BF16
-    const uint8_t cnew = active ? (uint8_t)N[jj] : (uint8_t)0;
-    if (jrec) {
-      // drawing the marks here (small problems): every record, J or zero, with
-      // no read of the previous count; otherwise only the stale records
-      if (MARKS && jrec_marks)
-        jrec[row] = active ? make_float4(J[jj][0], J[jj][1], J[jj][2], J[jj][3])
-                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      else if (cnew == 0 && counts[row] != 0)
-        jrec[row] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    }
-    counts[row] = cnew;
+    if (MARKS && jrec && jrec_marks)  // dense records: J, or zero without a jump
+      jrec[row] = active ? make_float4(J[jj][0], J[jj][1], J[jj][2], J[jj][3]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (DBG && active) {
       const size_t rk = (size_t)j * P.K + k;
       if (dbg_counts) dbg_counts[rk] = (uint8_t)N[jj];
@@ -463,71 +465,54 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
 
 // ---------------------------------------------------------------------------
 // Split form, part 1b (state-channel jumps).  marks_kernel: the marks of every
-// step whose count is positive, with the lanes of a warp busy on jumps
-// rather than on steps.  A warp covers 1024 consecutive rollouts of one step
-// j (two 16-byte loads of counts per lane), lists the jumping steps in shared
-// memory (a ballot prefix sum: deterministic positions) and draws each one's
-// summed marks on one lane (draw_marks, streams 2+n, as every other form
-// does), writing J into the step's jump record.  At the large workload's jump
-// probability (2.5 % per step) a warp lists about 26 steps: one pass of its
-// lanes.  Grid (ceil(Kpad / 4096), T), kMarkThreads threads.
+// (step, rollout) whose jump mask bit is set, with the lanes of a warp busy on
+// jumps rather than on steps.  A warp covers one 32-rollout row of the masks
+// over 32 steps (lane i loads the word of step 32c + i), lists the set bits in
+// shared memory (a ballot prefix sum: deterministic positions) and handles one
+// jump per lane: the step's count again from its Philox block (stream 1, as
+// in the noise pass), its summed marks (draw_marks, streams 2+n, as every
+// other form draws them) into the step's jump record.  At the large
+// workload's jump probability (2.5 % per step) a warp lists about 26 jumps:
+// one pass of its lanes.  Grid (ceil(Kpad / (32 * kMarkWarps)),
+// ceil(T / 32)), 32 * kMarkWarps threads.
 // ---------------------------------------------------------------------------
-constexpr int kMarkThreads = 128;
-constexpr int kMarkSpan = 1024;  // rollouts per warp
+constexpr int kMarkWarps = 4;
+constexpr int kMarkThreads = 32 * kMarkWarps;
 
 static __global__ void __launch_bounds__(kMarkThreads)
 marks_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t it_off,
-             const uint8_t* __restrict__ counts, float4* __restrict__ jrec, int* __restrict__ status) {
-  __shared__ uint32_t list[kMarkThreads / 32][kMarkSpan];
-  MJ_CHECK(blockDim.x == kMarkThreads && (int)blockIdx.y < P.T && P.Kpad % 32 == 0, status);
-  const int j = blockIdx.y;
+             const uint32_t* __restrict__ jmask, float4* __restrict__ jrec, int* __restrict__ status) {
+  __shared__ uint16_t list[kMarkWarps][1024];
+  MJ_CHECK(blockDim.x == kMarkThreads && 32 * (int)blockIdx.y < P.T && P.Kpad % 32 == 0, status);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int kw = (blockIdx.x * (kMarkThreads / 32) + w) * kMarkSpan;  // the warp's first rollout
-  const int kt = kw + 32 * lane;
-  uint32_t wd[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-  // Kpad is a multiple of 32, so kt < Kpad keeps all 32 bytes in the row
-  if (kt < P.Kpad) {
-    const uint4* src = reinterpret_cast<const uint4*>(counts + (size_t)j * P.Kpad + kt);
-    const uint4 a = src[0], b = src[1];
-    wd[0] = a.x; wd[1] = a.y; wd[2] = a.z; wd[3] = a.w;
-    wd[4] = b.x; wd[5] = b.y; wd[6] = b.z; wd[7] = b.w;
-  }
-  // bit 7 of each byte of nzw[q] is set when that count byte is nonzero
-  uint32_t nzw[8];
-  int ne = 0;  // 0 .. 32
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    nzw[q] = (((wd[q] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | wd[q]) & 0x80808080u;
-    ne += __popc(nzw[q]);
-  }
+  const int row = blockIdx.x * kMarkWarps + w;  // the warp's 32 rollouts: 32 row .. 32 row + 31
+  const int j = 32 * (int)blockIdx.y + lane;    // this lane's step
+  if (row >= P.Kpad / 32) return;               // the same for every lane of the warp
+  const uint32_t word = j < P.T ? jmask[(size_t)row * mask_cols(P.T) + j] : 0u;
+  const int ne = __popc(word);  // 0 .. 32
   uint32_t bal[6];
 #pragma unroll
-  for (int b = 0; b < 6; ++b) bal[b] = __ballot_sync(0xffffffffu, (ne >> b) & 1);
+  for (int q = 0; q < 6; ++q) bal[q] = __ballot_sync(0xffffffffu, (ne >> q) & 1);
   const uint32_t lt = (1u << lane) - 1u;
   int total = 0, pos = 0;
 #pragma unroll
-  for (int b = 0; b < 6; ++b) {
-    total += __popc(bal[b]) << b;
-    pos += __popc(bal[b] & lt) << b;
+  for (int q = 0; q < 6; ++q) {
+    total += __popc(bal[q]) << q;
+    pos += __popc(bal[q] & lt) << q;
   }
   if (total == 0) return;  // the same for every lane of the warp
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    uint32_t m = nzw[q];
-    while (m) {  // this lane's jumping steps, in rollout order
-      const int byte = (__ffs(m) - 1) >> 3;
-      list[w][pos++] = ((uint32_t)(32 * lane + 4 * q + byte) << 5) | ((wd[q] >> (8 * byte)) & 0xffu);
-      m &= m - 1u;
-    }
-  }
+  for (uint32_t mw = word; mw; mw &= mw - 1u)  // this lane's jumps, in rollout order
+    list[w][pos++] = (uint16_t)((lane << 5) | (__ffs(mw) - 1));
   __syncwarp();
   const uint32_t it = __ldg(it_ptr) + it_off;
   for (int e = lane; e < total; e += 32) {
     const uint32_t ev = list[w][e];
-    const int k = kw + (int)(ev >> 5), c = (int)(ev & 31u);
+    const int js = 32 * (int)blockIdx.y + (int)(ev >> 5), k = 32 * row + (int)(ev & 31u);
+    const uint32_t uk = P.k_base + (uint32_t)k;
+    const int c = jump_count(P, word_of(philox4x32_10(uk, (uint32_t)(js >> 2), it, 1u, P.key0, P.key1), js & 3));
     float J[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    draw_marks(P, P.k_base + (uint32_t)k, (uint32_t)j, it, c, J);
-    jrec[(size_t)j * P.Kpad + k] = make_float4(J[0], J[1], J[2], J[3]);
+    draw_marks(P, uk, (uint32_t)js, it, c, J);
+    jrec[(size_t)js * P.Kpad + k] = make_float4(J[0], J[1], J[2], J[3]);
   }
 }
 
@@ -536,14 +521,17 @@ marks_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
 // sequential dynamics from the stored step data.  A register ring of kAhead
 // slots keeps the loads of step j + kAhead in flight while step j is
 // computed (the loop is unrolled by kAhead so every slot index is static);
-// kAhead is the tile's "steps per unrolled chunk".  State-channel jumps add
-// the step's jump record (zero without a jump) on every step.
+// kAhead is the tile's "steps per unrolled chunk".  State-channel jumps add the
+// step's jump record (dense records: zero without a jump; sparse: loaded only
+// where the warp's mask word of the step, one broadcast load, has the lane's
+// bit, zero elsewhere).
 // ---------------------------------------------------------------------------
 template <int SYS, bool BF16, int kAhead>
 __global__ void __launch_bounds__(kRolloutThreads)
 rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
-                     const void* __restrict__ noise, const float4* __restrict__ jrec,
-                     float* __restrict__ s_part, uint32_t* __restrict__ rho_key, int* __restrict__ status) {
+                     const void* __restrict__ noise, const uint32_t* __restrict__ jmask,
+                     const float4* __restrict__ jrec, float* __restrict__ s_part, uint32_t* __restrict__ rho_key,
+                     int* __restrict__ status) {
   constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
   MJ_CHECK(blockDim.x % 32 == 0 && blockDim.x <= kRolloutThreads && P.Kpad % 32 == 0 && P.m == m, status);
   griddep_launch_dependents();
@@ -553,6 +541,8 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
   const bool active = k < P.K;
   const int T = active ? P.T : 0;  // padding lanes skip the loop
   const bool sj = P.jump_channel == 0;
+  const uint32_t* mrow = sj && jmask ? jmask + (size_t)(k >> 5) * mask_cols(P.T) : nullptr;
+  const uint32_t lane_bit = 1u << (k & 31);
   float x[n];
 #pragma unroll
   for (int i = 0; i < n; ++i) x[i] = __ldg(x0 + i);
@@ -573,7 +563,8 @@ rollout_split_kernel(const DevProblem P, const float* __restrict__ x0, const flo
 #pragma unroll
       for (int i = 0; i < m; ++i) u[i] = __ldg(U + step * m + i);
     }
-    jr = sj ? __ldg(jrec + row) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    jr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (sj && (!mrow || (__ldg(mrow + step) & lane_bit))) jr = __ldg(jrec + row);
   };
 #pragma unroll
   for (int sl = 0; sl < kAhead; ++sl)
@@ -636,6 +627,16 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// One 16-byte copy global -> shared (dst, src 16-byte aligned), completed
+// asynchronously; cp_async_arrive makes an mbarrier track this thread's
+// earlier copies (one pending arrival, released when they have landed).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -666,14 +667,25 @@ constexpr int kStatusTimeout = 4;               // MPPI_ETIMEOUT
 // Split form, part 2, staged.  rollout_staged_kernel: the same per-rollout
 // sequential dynamics as rollout_split_kernel, but the step data of the
 // block's rollouts (delta_eff rows, the control rows and, for state-channel
-// jumps, the jump-record rows) is moved into shared memory by the bulk-copy
-// engine, S steps per stage, two stage buffers.  The block is nt compute
-// threads (one per rollout) plus one producer warp.
+// jumps, the jump records) is moved into shared memory, S steps per stage,
+// two stage buffers.  The block is nt compute threads (one per rollout) plus
+// one producer warp.
 //
 // Each stage buffer has a "landed" mbarrier (its copies are complete) and an
 // "empty" one (every compute warp is done with it).  The producer's lane 0
-// issues the copies of stage s + 2 into a buffer once its compute warps have
-// released it from stage s.  A compute warp waits for "landed", runs its S
+// issues the bulk copies of stage s + 2 into a buffer once its compute warps
+// have released it from stage s.  State-channel jump records come in one of
+// two forms.  Dense (jmask == NULL, the records of every step written, zero
+// without a jump): lane 0 bulk-copies the record rows with the rest.  Sparse
+// (jmask != NULL, records valid only where the mask bit is set; the large
+// problems, where a jump is 2.5 % of the steps and dense rows would double
+// the bytes the rollout reads): each producer lane takes mask words (32
+// rollouts x one step, loaded a stage ahead), zeroes the slots whose bit was
+// set when the buffer was last filled, issues one 16-byte cp.async per set
+// bit into the rollout's slot and makes "landed" track its copies; lane 0's
+// second arrival on "landed" follows them.  Either way every slot holds the
+// step's record or zero.  The sparse gather of stage 0 is issued before the
+// wait on the previous kernel.  A compute warp waits for "landed", runs its S
 // steps from shared memory, releases the buffer and moves on; no compute
 // thread issues a copy or waits for another, and the dependency chain of the
 // dynamics never waits on a global load.  For block b the rows are
@@ -682,8 +694,8 @@ constexpr int kStatusTimeout = 4;               // MPPI_ETIMEOUT
 // every copy is 16-byte aligned and a multiple of 16 bytes).  The
 // control-row copy is rounded up to 16 bytes and may read up to 12 bytes past
 // U's end (U must sit in an allocation padded to 16 bytes).  A compute thread
-// adds s_J * J from its jump record on every step (the record is zero for a
-// step without a jump), so the step loop has no branch.  Every wait is
+// adds s_J * J from its jump-record slot on every step (zero for a step
+// without a jump), so the step loop has no branch.  Every wait is
 // bounded.  Launch with nt + 32 threads and staged_smem_total() bytes of
 // dynamic shared memory.
 // ---------------------------------------------------------------------------
@@ -693,8 +705,10 @@ constexpr int kStagedMaxThreads = kRolloutThreads + 32;
 // loop carries only what the problem needs):
 //   kJumpNone    jumps act on the controls (folded into delta_eff);
 //   kJumpDefault state jumps on the plant's velocity rows;
-//   kJumpRows    state jumps on any other rows.
-constexpr int kJumpNone = 0, kJumpDefault = 1, kJumpRows = 2;
+//   kJumpRows    state jumps on any other rows;
+// and for state jumps whether their records are dense (the two above) or
+// sparse (kJumpDefaultSparse, kJumpRowsSparse: gathered by jump mask).
+constexpr int kJumpNone = 0, kJumpDefault = 1, kJumpRows = 2, kJumpDefaultSparse = 3, kJumpRowsSparse = 4;
 
 // Shared-memory layout of the staged rollout (bytes), shared with the host:
 // two stage buffers, four mbarriers and the partial record's scratch (PART).
@@ -722,11 +736,14 @@ __host__ __device__ constexpr uint32_t staged_smem_total(int nt, int m, int sb, 
 template <int SYS, bool BF16, int S, int JM, bool PART>
 __global__ void __launch_bounds__(kStagedMaxThreads, PART ? 4 : 0)
 rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const float* __restrict__ U,
-                      const void* __restrict__ noise, const float4* __restrict__ jrec,
-                      float* __restrict__ s_part, uint32_t* __restrict__ rho_key, int* __restrict__ status,
-                      float* __restrict__ rec) {
+                      const void* __restrict__ noise, const uint32_t* __restrict__ jmask,
+                      const float4* __restrict__ jrec, float* __restrict__ s_part, uint32_t* __restrict__ rho_key,
+                      int* __restrict__ status, float* __restrict__ rec) {
   constexpr int n = Plant<SYS>::n, m = Plant<SYS>::m;
   constexpr bool kJ = JM != kJumpNone;
+  constexpr bool kSparse = JM == kJumpDefaultSparse || JM == kJumpRowsSparse;
+  constexpr bool kVelocityRows = JM == kJumpDefault || JM == kJumpDefaultSparse;
+  static_assert(S == 4 || S == 8 || S == 16, "a stage's mask words: at most 2 per producer lane");
   constexpr uint32_t SB = BF16 ? 2u : 4u;
   extern __shared__ __align__(128) unsigned char stage_smem[];
   const int nt = blockDim.x - 32, tid = threadIdx.x;  // compute threads, then the producer warp
@@ -751,9 +768,17 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
            status);
 
   griddep_launch_dependents();
+  if constexpr (kSparse) {
+    // every jump-record slot of both buffers starts at zero
+    for (uint32_t i = tid; i < 2u * S * nt; i += blockDim.x)
+      reinterpret_cast<float4*>(stage_smem + (i / (S * nt)) * stage_bytes + t_off)[i % (S * nt)] =
+          make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
   if (tid == nt) {
-    mbar_init(landed, 1);
-    mbar_init(landed + 1, 1);
+    // landed: lane 0's arrival with the byte count and, sparse, its arrival
+    // after the lanes' record copies were issued
+    mbar_init(landed, kSparse ? 2 : 1);
+    mbar_init(landed + 1, kSparse ? 2 : 1);
     mbar_init(empty, (uint32_t)compute_warps);
     mbar_init(empty + 1, (uint32_t)compute_warps);
     mbar_init_fence();
@@ -776,8 +801,8 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
   int issued = 0;  // stages whose copies the producer issued
   bool ok = true;
 
-  if (tid >= nt) {
-    // ---- producer warp: lane 0 issues every stage's copies
+  if (tid >= nt && !kSparse) {
+    // ---- producer warp, dense records: lane 0 issues every stage's copies
     if (!PART && tid != nt) return;
     if (tid == nt) {
       const uint32_t j_bytes = kJ ? (uint32_t)nk * 16u : 0u;
@@ -817,6 +842,84 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
       }
     }
     issued = __shfl_sync(0xffffffffu, issued, 0);
+  } else if (kSparse && tid >= nt) {
+    // ---- producer warp, sparse records: lane 0 issues every stage's bulk
+    // copies, every lane gathers records
+    const int lane = tid - nt;
+    const int mrows = nk >> 5;  // mask rows (32 rollouts each) of this block
+    // the lane's mask words of a stage: pair p = lane + 32 r is row p / S, step p % S
+    auto load_masks = [&](int st, uint32_t& w0, uint32_t& w1) {
+      const int j0 = st * S, ns = min(S, T - j0);
+      const uint32_t* mb = jmask + (size_t)(k0 >> 5) * mask_cols(T) + j0;
+      const int p0 = lane, p1 = lane + 32;
+      w0 = (p0 / S < mrows && p0 % S < ns) ? __ldg(mb + (size_t)(p0 / S) * mask_cols(T) + p0 % S) : 0u;
+      w1 = (p1 / S < mrows && p1 % S < ns) ? __ldg(mb + (size_t)(p1 / S) * mask_cols(T) + p1 % S) : 0u;
+    };
+    uint32_t cur0 = 0, cur1 = 0;              // masks of the stage being issued
+    uint32_t oa0 = 0, oa1 = 0, ob0 = 0, ob1 = 0;  // masks last gathered into buffer 0 / 1
+    // sparse: the record slots of pair p, zero where only the old mask is
+    // set, a copy where the new one is
+    auto gather = [&](int p, int j0, unsigned char* base, uint32_t nw, uint32_t ow) {
+      unsigned char* slot = base + t_off + (p % S) * j_stride + (p / S) * 32 * 16;
+      for (uint32_t z = ow & ~nw; z; z &= z - 1u)
+        *reinterpret_cast<float4*>(slot + (__ffs(z) - 1) * 16) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float4* src = jrec + (size_t)(j0 + p % S) * P.Kpad + k0 + (p / S) * 32;
+      for (uint32_t z = nw; z; z &= z - 1u) cp_async16(slot + (__ffs(z) - 1) * 16, src + (__ffs(z) - 1));
+    };
+    for (int st = 0; st < n_stages && ok; ++st) {
+      const int buf = st & 1;
+      if (st >= 2) {
+        // every compute warp released the buffer (use st/2 - 1 of it)
+        if (lane == 0) ok = mbar_wait_bounded(empty + buf, (uint32_t)((st >> 1) - 1) & 1u, kCopyWaitNs);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        __syncwarp();  // the lanes' slot writes come after the compute warps' reads
+        if (lane == 0) fence_async_smem();
+      }
+      const int j0 = st * S;
+      const int ns = min(S, T - j0);
+      unsigned char* base = stage_smem + buf * stage_bytes;
+      const uint32_t u_bytes = ((uint32_t)ns * m * 4 + 15) & ~15u;
+      if (lane == 0) {
+        mbar_expect_tx(landed + buf, (uint32_t)ns * d_bytes + u_bytes);
+        issue_delta(st, j0, ns);
+      }
+      if constexpr (kSparse) {
+        if (st == 0) load_masks(0, cur0, cur1);
+        gather(lane, j0, base, cur0, buf ? ob0 : oa0);
+        gather(lane + 32, j0, base, cur1, buf ? ob1 : oa1);
+        if (buf) {
+          ob0 = cur0;
+          ob1 = cur1;
+        } else {
+          oa0 = cur0;
+          oa1 = cur1;
+        }
+        cp_async_arrive(landed + buf);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(landed + buf);
+        if (st + 1 < n_stages) load_masks(st + 1, cur0, cur1);
+      }
+      if (lane == 0) {
+        // the step data was drawn before the previous kernel; the controls
+        // come from the previous update
+        if (st == 0) griddep_wait();
+        bulk_load(base + u_off, U + (size_t)j0 * m, u_bytes, landed + buf);
+      }
+      ++issued;
+    }
+    cp_async_wait_all();
+    if (!ok && lane == 0) {
+      atomicExch(status, kStatusTimeout);
+      if (PART) *abort_flag = 1;
+    }
+    if (!PART) {
+      // leave only when the copies of the last two stages have landed (bounded)
+      if (lane == 0)
+        for (int ls = max(0, issued - 2); ls < issued; ++ls)
+          mbar_wait_bounded(landed + (ls & 1), (uint32_t)(ls >> 1) & 1u, kCopyWaitNs);
+      return;
+    }
   } else {
     // ---- compute threads: one rollout each
     const int k = k0 + tid;
@@ -867,7 +970,7 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
           if constexpr (kJ) {
             const float4 jr = reinterpret_cast<const float4*>(base + t_off + jj * j_stride)[tid];
             const float J[4] = {jr.x, jr.y, jr.z, jr.w};  // zero for a step without a jump
-            if constexpr (JM == kJumpDefault) state_jump_default<SYS>(P, x, J);
+            if constexpr (kVelocityRows) state_jump_default<SYS>(P, x, J);
             else state_jump_rows<SYS>(P, x, J);
           }
         }
@@ -941,6 +1044,7 @@ rollout_staged_kernel(const DevProblem P, const float* __restrict__ x0, const fl
             if (ts >= 2) fence_async_smem();
             const int j0 = ts * S, ns = min(S, T - j0);
             mbar_expect_tx(landed + (g & 1), (uint32_t)ns * d_bytes);
+            if (kSparse) mbar_arrive(landed + (g & 1));  // no records in this pass
             issue_delta(g, j0, ns);
             issued = g + 1;
           }

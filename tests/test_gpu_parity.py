@@ -117,6 +117,37 @@ def test_non_default_jump_rows_every_tile_matches_oracle(cuda, name, tile):
     _record(f"{name}_tile{tile}", rep)
 
 
+def _sparse_cases():
+    """State-jump problems with more rollout blocks of 128 than a GB300 has
+    SMs (152), where the jump records are sparse (jump masks, marks drawn by
+    the lanes of a warp on jumps, records gathered by the rollout): a ragged K
+    and a horizon that ends inside a stage, default and other jump rows."""
+    c = {}
+    p = W.quadrotor_k4096(K=24577, T=40, nu=10.0, lam=20.0, name="quadrotor_K24577_T40_sparse")
+    r = np.random.default_rng(30)
+    c["quadrotor_K24577_T40"] = (p, W.random_state(p, r, 0.1), W.random_controls(p, r, 0.2), 3)
+    p = W.cartpole_k1000(K=20001, T=33, nu=10.0, jump_rows=[0, 2], noise_dtype="bf16",
+                         name="cartpole_rows02_K20001_T33_sparse")
+    r = np.random.default_rng(31)
+    c["cartpole_rows02_K20001_T33_bf16"] = (p, W.random_state(p, r), W.random_controls(p, r), 11)
+    return c
+
+
+SPARSE_CASES = _sparse_cases()
+
+
+@pytest.mark.parametrize("tile", [None, (2, 128, 4), (2, 64, 8), (3, 128, 16), (3, 64, 4), (3, 96, 8),
+                                  (4, 128, 8), (4, 96, 16)],
+                         ids=["default", "split", "split_64", "staged_long", "staged_64_short",
+                              "staged_96", "block_records", "block_records_96"])
+@pytest.mark.parametrize("name", list(SPARSE_CASES))
+def test_sparse_jump_records_every_tile_match_oracle(cuda, name, tile):
+    prob, x0, U, it = SPARSE_CASES[name]
+    rep = parity.run_and_compare(prob, x0, U, it, tile=tile)
+    assert rep["jumps"] > 10000
+    _record(f"{name}_tile{tile}", rep)
+
+
 @pytest.mark.parametrize("tile", [None, (4, 128, 8)], ids=["default", "block_records"])
 def test_large_quadrotor_sampled_and_full_update(cuda, tile):
     """K=65536, T=200, dt=0.005, Laplace marks at 5/s, bfloat16 noise: every
