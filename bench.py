@@ -363,11 +363,15 @@ def _config(prob, solves_per_s):
 # One single-problem workload
 # --------------------------------------------------------------------------
 
-def _launches_per_iteration(prob, tile):
+def _launches_per_iteration(prob, tile, n_sms):
+    """Kernels of one iteration: the fused tile's rollout and update; else the
+    noise pass, the rollout and the update, plus the marks pass for sparse
+    state-jump records (rollout blocks of 128 beyond the SM count)."""
     if tile[0] == 1:
         return 2
-    marks = prob["jump_channel"] == "state" and prob["nu"] > 0
-    return 4 if marks else 3
+    sparse = (prob["jump_channel"] == "state" and prob["nu"] > 0
+              and (prob["K"] + 127) // 128 > n_sms)
+    return 4 if sparse else 3
 
 
 def measure_workload(prob, args, steps, warmup, clk, dist, ws, local):
@@ -508,7 +512,7 @@ def measure_workload(prob, args, steps, warmup, clk, dist, ws, local):
         # per iteration: noise (+ marks for state-channel jumps) + rollout +
         # update (split and staged tiles) or rollout + update (fused tile),
         # timed region A only
-        "gpu_launches": _launches_per_iteration(prob, tile) * iters * steps,
+        "gpu_launches": _launches_per_iteration(prob, tile, n_sms) * iters * steps,
         "roofline": {"bound": "alu", "kernel": rk,
                      "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
                      "frac": achieved / alu_peak,

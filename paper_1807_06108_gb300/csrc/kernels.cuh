@@ -429,27 +429,38 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
     if ((threadIdx.x & 31) == 0)
       reinterpret_cast<uint4*>(jmask + (size_t)(k >> 5) * mask_cols(P.T))[b] = mw;
   }
-  float zc[4];
-  if constexpr (M == 1) normals4(philox4x32_10(uk, (uint32_t)b, it, 0u, P.key0, P.key1), zc);
+  // The four steps' perturbations first, as independent dependency chains
+  // (the four Philox blocks of the steps interleave); a thread of the last
+  // step block with fewer than four steps draws the missing ones and drops
+  // them.
+  float de[4][M];
+  if constexpr (M == 1) {
+    float zc[4];
+    normals4(philox4x32_10(uk, (uint32_t)b, it, 0u, P.key0, P.key1), zc);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) de[jj][0] = __fmul_rn(P.sqc_sigma[0], zc[jj]);
+  } else {
+    uint4 w[4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) w[jj] = philox4x32_10(uk, (uint32_t)(4 * b + jj), it, 0u, P.key0, P.key1);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      float z[4];
+      normals4(w[jj], z);
+#pragma unroll
+      for (int i = 0; i < M; ++i) de[jj][i] = __fmul_rn(P.sqc_sigma[i], z[i]);
+    }
+  }
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj) {
     const int j = 4 * b + jj;
     if (jj >= ns) break;
-    float de[M];
-    if constexpr (M == 1) {
-      de[0] = __fmul_rn(P.sqc_sigma[0], zc[jj]);
-    } else {
-      float z[4];
-      normals4(philox4x32_10(uk, (uint32_t)j, it, 0u, P.key0, P.key1), z);
-#pragma unroll
-      for (int i = 0; i < M; ++i) de[i] = __fmul_rn(P.sqc_sigma[i], z[i]);
-    }
     const size_t row = (size_t)j * P.Kpad + k;
     if (MARKS && P.jump_channel == 1 && N[jj] > 0) {
 #pragma unroll
-      for (int i = 0; i < M; ++i) de[i] = __fadd_rn(de[i], J[jj][i]);
+      for (int i = 0; i < M; ++i) de[jj][i] = __fadd_rn(de[jj][i], J[jj][i]);
     }
-    store_noise<M, BF16>(noise, row, de, active);  // rounds to bfloat16 (RNE) when BF16
+    store_noise<M, BF16>(noise, row, de[jj], active);  // rounds to bfloat16 (RNE) when BF16
     if (MARKS && jrec && jrec_marks)  // dense records: J, or zero without a jump
       jrec[row] = active ? make_float4(J[jj][0], J[jj][1], J[jj][2], J[jj][3]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (DBG && active) {
