@@ -463,7 +463,10 @@ def measure_workload(prob, args, steps, warmup, clk, dist, ws, local):
     # ---- region D: the update kernel on its own (same launch configuration):
     # inside the step it shares the GPU with the next iteration's noise pass,
     # which blurs its bandwidth figure.  Each launch follows a fresh
-    # rollout_cost (which arms the running minimum) and an L2 flush.
+    # rollout_cost (which arms the running minimum) and an L2 flush: a write
+    # of twice the L2 size, then a read of it, so that the flush's dirty lines
+    # are written back before the timed launch rather than during it (a cold,
+    # clean L2, as under ncu's cache control).
     n_iso = min(steps, 50)
     iso_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(n_iso)]
@@ -471,6 +474,7 @@ def measure_workload(prob, args, steps, warmup, clk, dist, ws, local):
         solver.rollout_cost(x0, want_costs=False)
         with torch.cuda.stream(stream):
             flush.fill_(float(i))
+            flush.sum()
             if i >= 3:
                 iso_ev[i - 3][0].record(stream)
             mppi.mppi_jump_update(ctx)
@@ -526,7 +530,7 @@ def measure_workload(prob, args, steps, warmup, clk, dist, ws, local):
                             "avg_launch_ms": upd_iso_ms, "algorithmic_bytes": upd_bytes,
                             "in_step_avg_launch_ms": upd_avg,
                             "traffic": _traffic(prob["name"], "update_kernel"),
-                            "note": f"{peak_kind} copy bandwidth; timed alone after an L2 flush "
+                            "note": f"{peak_kind} copy bandwidth; timed alone after an L2 flush and clean "
                                     "(in the step it overlaps the next noise pass)"},
     }
 
