@@ -77,32 +77,34 @@ __device__ __forceinline__ float uniform01(uint32_t w) {
   return fmaf(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
 }
 
-// sin(2 pi u) and cos(2 pi u) for the uniforms above.  8u is exact; its
-// integer part q (0..7) is the octant and its fraction f (exact) places the
-// angle (pi/4) g within it, g = f (even octants) or 1 - f (odd octants,
-// exact), so that sin and cos of (pi/4) g, g in [0, 1], cover every octant
-// through the symmetries sin(pi/2 - a) = cos a, sin(pi + a) = -sin a.  They
-// come from their Taylor series in g, to degree 9 and 10 (truncation below
-// 3e-9); the coefficients are (pi/4)^n / n! with alternating signs.  Over all
-// 2^23 uniforms the float32 result is within 1.1 ulp of sin and cos (checked
-// against a double-precision evaluation).
+// sin(2 pi u) and cos(2 pi u) for the uniforms above.  With x = 4u (exact),
+// the nearest integer q of x (adding and subtracting 1.5 * 2^23 rounds it,
+// and the low two bits of the sum's encoding are q mod 4) is the quadrant and
+// f = x - q in [-1/2, 1/2] (exact) places the angle (pi/2) f within it, so
+// that sin(q pi/2 + a) and cos(q pi/2 + a) come from sin a and cos a by a
+// swap (q odd) and sign flips (q mod 4 in {2, 3} for sin, {1, 2} for cos).
+// sin a and cos a, |a| <= pi/4, come from their Taylor series in f, to
+// degree 9 and 10 (truncation below 3e-9); the coefficients are
+// (pi/2)^n / n! with alternating signs.  Over all 2^23 uniforms the float32
+// result is within 1.7 ulp of sin and cos (checked against a double-precision
+// evaluation).
 __device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
-  constexpr float kS1 = 0.785398163397448f, kS3 = -0.0807455121882808f, kS5 = 0.00249039457019272f,
-                  kS7 = -3.65762041821772e-05f, kS9 = 3.13361689037812e-07f;
-  constexpr float kC2 = -0.308425137534042f, kC4 = 0.0158543442438155f, kC6 = -0.00032599188692739f,
-                  kC8 = 3.59086044859151e-06f, kC10 = -2.4611369504942e-08f;
-  const float x = 8.0f * u;
-  const float xq = floorf(x);
-  const int q = (int)xq;
-  const float f = x - xq;
-  const float g = (q & 1) ? 1.0f - f : f;
-  const float g2 = g * g;
-  const float sp = g * fmaf(g2, fmaf(g2, fmaf(g2, fmaf(g2, kS9, kS7), kS5), kS3), kS1);
-  const float cp = fmaf(g2, fmaf(g2, fmaf(g2, fmaf(g2, fmaf(g2, kC10, kC8), kC6), kC4), kC2), 1.0f);
-  const bool swap = ((q + 1) & 2) != 0;  // octants 1, 2, 5, 6
-  const float sv = swap ? cp : sp, cv = swap ? sp : cp;
-  s = q >= 4 ? -sv : sv;
-  c = (q >= 2 && q <= 5) ? -cv : cv;
+  constexpr float kS1 = 1.57079637050628662f, kS3 = -0.645964086055755615f, kS5 = 0.0796926245093345642f,
+                  kS7 = -0.00468175392597913742f, kS9 = 0.000160441180923953652f;
+  constexpr float kC2 = -1.23370051383972168f, kC4 = 0.253669500350952148f, kC6 = -0.0208634808659553528f,
+                  kC8 = 0.000919260259252041578f, kC10 = -2.52020417974563315e-05f;
+  constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+  const float x = 4.0f * u;
+  const float y = __fadd_rn(x, kRound);
+  const float f = __fsub_rn(x, __fsub_rn(y, kRound));
+  const uint32_t q = __float_as_uint(y);
+  const float f2 = f * f;
+  const float sp = f * fmaf(f2, fmaf(f2, fmaf(f2, fmaf(f2, kS9, kS7), kS5), kS3), kS1);
+  const float cp = fmaf(f2, fmaf(f2, fmaf(f2, fmaf(f2, fmaf(f2, kC10, kC8), kC6), kC4), kC2), 1.0f);
+  const bool odd = (q & 1u) != 0u;
+  const float sv = odd ? cp : sp, cv = odd ? sp : cp;
+  s = __uint_as_float(__float_as_uint(sv) ^ ((q << 30) & 0x80000000u));
+  c = __uint_as_float(__float_as_uint(cv) ^ (((q + 1u) << 30) & 0x80000000u));
 }
 
 // Box-Muller (1958): r = sqrt(-2 ln u_a), (r cos 2 pi u_b, r sin 2 pi u_b).
