@@ -452,6 +452,20 @@ cudaError_t launch_update(const DevProblem& P, const IterBuffers& b, const Updat
   a.it_advance = it_advance;
   a.shift = a.export_out ? 0 : shift;
   for (int i = 0; i < 4; ++i) a.u_init[i] = P.u_init[i];
+  const size_t delta_bytes = (size_t)P.T * P.Kpad * P.m * (P.noise_bf16 ? 2 : 4);
+  if (!records && !a.export_out && P.Kpad <= kSmallMaxK && P.T * P.m <= kSmallMaxTM &&
+      delta_bytes <= kSmallMaxBytes) {
+    // one block does the whole update (update_small_kernel)
+    const dim3 grid(1), block(kSmallThreads);
+    if (P.m == 4) {
+      if (P.noise_bf16) launch_hi(update_small_kernel<true, 4>, grid, block, 0, s, false, a);
+      else launch_hi(update_small_kernel<false, 4>, grid, block, 0, s, false, a);
+    } else {
+      if (P.noise_bf16) launch_hi(update_small_kernel<true, 1>, grid, block, 0, s, false, a);
+      else launch_hi(update_small_kernel<false, 1>, grid, block, 0, s, false, a);
+    }
+    return cudaGetLastError();
+  }
   if (P.m == 4) {
     if (P.noise_bf16) launch_update_m<true, 4>(a, g, records, s);
     else launch_update_m<false, 4>(a, g, records, s);

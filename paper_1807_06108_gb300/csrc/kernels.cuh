@@ -1692,6 +1692,154 @@ __global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateA
   if (threadIdx.x == 0) *a.done = 0u;
 }
 
+// Small problems (the perturbations of one iteration within kSmallMaxBytes,
+// Kpad <= kSmallMaxK, T*M <= kSmallMaxTM): the whole update (Eq. 35-37) in
+// one block of kSmallThreads threads, with no tickets and no partial sums in
+// global memory, so its latency is one pass over the perturbations rather
+// than a chain of barriers, atomics and second reads.  The block forms
+// e_k = exp(-(S~_k - rho)/lambda) for every rollout in shared memory with
+// their compensated sum Z, then each warp reduces whole rows j of delta_eff
+// (N_j[i] = sum_k e_k delta_eff[j][k][i], per-lane products, compensated
+// shuffle sums), and after a barrier every thread updates its entries of U
+// (U_j <- U_j + alpha N_j / Z; with the MPC shift, row j's value goes to row
+// j - 1, the first to u0, the last row to u_init).  Diagnostics, the status
+// word, the counter advance and the re-arming of the running minima as in
+// the one-launch update.  The plain source only (no records, no export).
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallMaxK = 8192;
+constexpr int kSmallMaxTM = 2048;
+constexpr size_t kSmallMaxBytes = 256u * 1024u;
+
+template <bool BF16, int M>
+__global__ void __launch_bounds__(kSmallThreads, 1) update_small_kernel(const UpdateArgs a) {
+  constexpr int NT = kSmallThreads;
+  constexpr int E = BF16 ? 8 : 4;  // elements per 16-byte vector
+  constexpr int RPV = E / M;       // rollouts per vector
+  constexpr int B = 4;             // 16-byte loads per lane in flight
+  __shared__ __align__(16) float e[kSmallMaxK];
+  __shared__ float nsum[kSmallMaxTM];
+  __shared__ float sh_s[NT / 32], sh_c[NT / 32];
+  MJ_CHECK(blockDim.x == NT && gridDim.x == 1 && gridDim.y == 1 && a.Kpad <= kSmallMaxK &&
+               a.T * M <= kSmallMaxTM && a.Kpad % 32 == 0 && !a.export_out && !a.rec,
+           a.status);
+  griddep_launch_dependents();
+  griddep_wait();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int TM = a.T * M;
+  if (a.rho_key_next && tid == 0) *a.rho_key_next = kKeyEmpty;
+  const uint32_t key = __ldcg(a.rho_key);
+  const bool ok = key < kKeyInf;  // at least one finite cost
+  const float rho = ok ? key_to_float(key) : 0.0f;
+  // the rollout-independent cost of the controls that were rolled out
+  const float C = control_cost_sum<M, NT>(a.U, a.T, a.lam, a.inv_sigma2, sh_s, sh_c);
+  float Z = 0.0f;
+  if (ok) {
+    float zs = 0.0f, zc = 0.0f;
+    for (int k = tid; k < a.Kpad; k += NT) {
+      const float ev = expf((rho - __ldcg(a.s_part + k)) * a.inv_lam);
+      e[k] = ev;
+      two_sum_acc(zs, zc, ev);
+    }
+    Z = block_sum2<NT>(zs, zc, sh_s, sh_c);  // its barriers publish e
+    const int nvec = a.Kpad * M / E;
+    const uint4* nv = reinterpret_cast<const uint4*>(a.noise);
+    for (int j = wid; j < a.T; j += NT / 32) {
+      const uint4* row = nv + (size_t)j * nvec;
+      float acc[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) acc[i] = 0.0f;
+      for (int base = 0; base < nvec; base += 32 * B) {
+        uint4 q[B];
+#pragma unroll
+        for (int h = 0; h < B; ++h) {
+          const int v = base + lane + 32 * h;
+          q[h] = v < nvec ? __ldcs(row + v) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int h = 0; h < B; ++h) {
+          const int v = base + lane + 32 * h;
+          if (v >= nvec) continue;
+          float val[E];
+          if constexpr (BF16) {
+            const uint32_t wd[4] = {q[h].x, q[h].y, q[h].z, q[h].w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              val[2 * t] = __uint_as_float(wd[t] << 16);
+              val[2 * t + 1] = __uint_as_float(wd[t] & 0xffff0000u);
+            }
+          } else {
+            val[0] = __uint_as_float(q[h].x);
+            val[1] = __uint_as_float(q[h].y);
+            val[2] = __uint_as_float(q[h].z);
+            val[3] = __uint_as_float(q[h].w);
+          }
+          float ew[RPV];  // the weights of the vector's rollouts
+          if constexpr (RPV == 1) {
+            ew[0] = e[v];
+          } else if constexpr (RPV == 2) {
+            const float2 t2 = reinterpret_cast<const float2*>(e)[v];
+            ew[0] = t2.x;
+            ew[1] = t2.y;
+          } else {
+#pragma unroll
+            for (int t = 0; t < RPV / 4; ++t) {
+              const float4 t4 = reinterpret_cast<const float4*>(e)[v * (RPV / 4) + t];
+              ew[4 * t] = t4.x;
+              ew[4 * t + 1] = t4.y;
+              ew[4 * t + 2] = t4.z;
+              ew[4 * t + 3] = t4.w;
+            }
+          }
+#pragma unroll
+          for (int q2 = 0; q2 < E; ++q2) acc[q2 % M] = fmaf(ew[q2 / M], val[q2], acc[q2 % M]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        float c = 0.0f;
+        warp_sum2(acc[i], c);
+        if (lane == 0) nsum[j * M + i] = acc[i] + c;
+      }
+    }
+    __syncthreads();
+    // every new value before any write: with the shift a row's value goes
+    // to the row before it
+    const float inv_Z = 1.0f / Z;
+    float v0 = 0.0f, v1 = 0.0f;
+    if (tid < TM) v0 = __ldcg(a.U + tid) + a.alpha * (nsum[tid] * inv_Z);
+    if (tid + NT < TM) v1 = __ldcg(a.U + tid + NT) + a.alpha * (nsum[tid + NT] * inv_Z);
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int idx = tid + h * NT;
+      const float v = h ? v1 : v0;
+      if (idx >= TM) continue;
+      if (a.shift) {
+        if (idx >= M) a.U[idx - M] = v;
+        else if (a.u0_out) a.u0_out[idx] = v;
+        if (idx >= TM - M) a.U[idx] = a.u_init[idx - (TM - M)];
+      } else {
+        a.U[idx] = v;
+      }
+    }
+  } else if (a.shift && a.u0_out && tid < M) {
+    a.u0_out[tid] = __ldcg(a.U + tid);
+  }
+  if (tid == 0) {
+    if (ok) {
+      const float rf = rho + C;
+      a.diag[0] = rf;
+      a.diag[1] = Z;
+      a.diag[2] = rf * a.inv_lam - logf(Z / (float)a.K);
+      a.diag[3] = rho;
+    } else {
+      *a.status = kStatusNonFinite;
+    }
+    *a.it = *a.it + a.it_advance;
+    *a.rho_key = kKeyEmpty;
+  }
+}
+
 // w_k = exp((rho - S~_k)/lambda) / Z for the weights getter (the e_k of the
 // update, normalised), from the costs and the diagnostics (Z, raw rho).
 static __global__ void weights_kernel(const float* __restrict__ s_part, const float* __restrict__ diag,
