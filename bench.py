@@ -363,6 +363,18 @@ def _config(prob, solves_per_s):
 # One single-problem workload
 # --------------------------------------------------------------------------
 
+def _update_kernel_name(prob, tile):
+    """The library runs the whole update in one block (update_small_kernel)
+    when the perturbations of an iteration fit in 256 KB, Kpad <= 8192 and
+    T*m <= 2048 (not with the block-record tile); update_kernel otherwise."""
+    m = 1 if prob["system"] == "cartpole" else 4
+    kpad = (prob["K"] + 31) // 32 * 32
+    sb = 2 if prob["noise_dtype"] == "bf16" else 4
+    small = (tile[0] != 4 and kpad <= 8192 and prob["T"] * m <= 2048
+             and prob["T"] * kpad * m * sb <= 256 * 1024)
+    return "update_small_kernel" if small else "update_kernel"
+
+
 def _launches_per_iteration(prob, tile, n_sms):
     """Kernels of one iteration: the fused tile's rollout and update; else the
     noise pass, the rollout and the update, plus the marks pass for sparse
@@ -505,6 +517,7 @@ def measure_workload(prob, args, steps, warmup, clk, dist, ws, local):
     upd_gbs = upd_bytes / (upd_iso_ms / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     rk = ROLLOUT_KERNELS[tile[0]]
+    uk = _update_kernel_name(prob, tile)
     return {
         "value": value, "ms_per_step": ms_per_step,
         "config": _config(prob, value / steps_per_solve) | {
@@ -525,11 +538,11 @@ def measure_workload(prob, args, steps, warmup, clk, dist, ws, local):
                      "peak_basis": f"{n_sms} SMs x 128 lanes x {sm_mhz:.0f} MHz "
                                    f"({peak_kind} max clock)",
                      "ops_per_trajectory_step": ops_step},
-        "roofline_update": {"bound": "hbm", "kernel": "update_kernel", "achieved": upd_gbs,
+        "roofline_update": {"bound": "hbm", "kernel": uk, "achieved": upd_gbs,
                             "peak": hbm, "unit": "GB/s", "frac": upd_gbs / hbm,
                             "avg_launch_ms": upd_iso_ms, "algorithmic_bytes": upd_bytes,
                             "in_step_avg_launch_ms": upd_avg,
-                            "traffic": _traffic(prob["name"], "update_kernel"),
+                            "traffic": _traffic(prob["name"], uk),
                             "note": f"{peak_kind} copy bandwidth; timed alone after an L2 flush and clean "
                                     "(in the step it overlaps the next noise pass)"},
     }
