@@ -29,6 +29,7 @@ struct DevProblem {
   int32_t jump_default;  // state jumps hit the plant's velocity rows (1, 3) / (3, 4, 5)
   int32_t jump_rows[4];
   uint32_t key0, key1;
+  uint32_t rk[20];  // Philox round keys: rk[2r] = key0 + r * 0x9E3779B9, rk[2r+1] = key1 + r * 0xBB67AE85
   uint32_t k_base;  // Philox index of local rollout 0 (a rollout shard starts at k_base)
   uint32_t thr[kMaxJumps];  // jump-count thresholds (see the header)
   float dt, lam, inv_lam, is_coef, alpha, s_jump;
@@ -67,6 +68,26 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
     c3 = lo0;
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// The same generator with the ten round keys precomputed (rk as in
+// DevProblem): in a kernel whose problem is a launch parameter they are
+// constant-bank operands of the XORs, and no key arithmetic is left per round.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                  const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+    const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
+    const uint32_t n0 = hi1 ^ c1 ^ rk[2 * r];
+    const uint32_t n2 = hi0 ^ c3 ^ rk[2 * r + 1];
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
   }
   return make_uint4(c0, c1, c2, c3);
 }

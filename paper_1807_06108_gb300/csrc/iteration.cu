@@ -90,6 +90,10 @@ mppi_status pack_problem(const mppi_jump_config* cfg, DevProblem* P, char* msg) 
   for (int c = 0; c < 4; ++c) P->jump_rows[c] = c < cfg->q ? cfg->jump_rows[c] : -1;
   P->key0 = (uint32_t)(cfg->seed & 0xffffffffull);
   P->key1 = (uint32_t)(cfg->seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    P->rk[2 * r] = P->key0 + (uint32_t)r * 0x9E3779B9u;
+    P->rk[2 * r + 1] = P->key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   P->dt = cfg->dt;
   P->lam = cfg->lambda;
   P->inv_lam = (float)(1.0 / (double)cfg->lambda);

@@ -388,7 +388,7 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
   const uint32_t it = __ldg(it_ptr) + it_off;
   const uint32_t uk = P.k_base + (uint32_t)k;  // the rollout's index in the Philox counter
   const int ns = min(4, P.T - 4 * b);  // steps of this thread
-  const uint4 wcount = philox4x32_10(uk, (uint32_t)b, it, 1u, P.key0, P.key1);
+  const uint4 wcount = philox4x32_10_rk(uk, (uint32_t)b, it, 1u, P.rk);
   int N[4];
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj) N[jj] = jj < ns ? jump_count(P, word_of(wcount, jj)) : 0;
@@ -436,13 +436,13 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
   float de[4][M];
   if constexpr (M == 1) {
     float zc[4];
-    normals4(philox4x32_10(uk, (uint32_t)b, it, 0u, P.key0, P.key1), zc);
+    normals4(philox4x32_10_rk(uk, (uint32_t)b, it, 0u, P.rk), zc);
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) de[jj][0] = __fmul_rn(P.sqc_sigma[0], zc[jj]);
   } else {
     uint4 w[4];
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) w[jj] = philox4x32_10(uk, (uint32_t)(4 * b + jj), it, 0u, P.key0, P.key1);
+    for (int jj = 0; jj < 4; ++jj) w[jj] = philox4x32_10_rk(uk, (uint32_t)(4 * b + jj), it, 0u, P.rk);
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       float z[4];
@@ -520,7 +520,7 @@ marks_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
     const uint32_t ev = list[w][e];
     const int js = 32 * (int)blockIdx.y + (int)(ev >> 5), k = 32 * row + (int)(ev & 31u);
     const uint32_t uk = P.k_base + (uint32_t)k;
-    const int c = jump_count(P, word_of(philox4x32_10(uk, (uint32_t)(js >> 2), it, 1u, P.key0, P.key1), js & 3));
+    const int c = jump_count(P, word_of(philox4x32_10_rk(uk, (uint32_t)(js >> 2), it, 1u, P.rk), js & 3));
     float J[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     draw_marks(P, uk, (uint32_t)js, it, c, J);
     jrec[(size_t)js * P.Kpad + k] = make_float4(J[0], J[1], J[2], J[3]);
