@@ -1229,7 +1229,9 @@ struct UpdateArgs {
 // the warp's first row, and the chunk's first costs S~_k.
 template <bool BF16, int M, int VPT, int NT>
 struct UpdatePrefetch {
-  static constexpr int kB = 4;                                         // 16-byte loads per lane in flight
+  // 16-byte loads per lane in flight: with one vector per thread a warp's
+  // whole row of the chunk (256 vectors) is one batch, loaded up front
+  static constexpr int kB = VPT == 1 ? 8 : 4;
   static constexpr int kWT = chunk_rollouts<BF16, M, VPT, NT>() / NT;  // costs per thread
   static constexpr int kWB = kWT < 8 ? kWT : 8;                        // of them, loaded up front
   uint4 q[kB];
@@ -1598,7 +1600,7 @@ __device__ __forceinline__ void update_final_body(const UpdateArgs& a, bool ok, 
 // rollouts); SRC = 1: it rescales and sums partial records (chunks of
 // records).
 template <bool BF16, int M, int VPT, int SRC>
-__global__ void __launch_bounds__(kUpdateThreads, 6) update_kernel(const UpdateArgs a) {
+__global__ void __launch_bounds__(kUpdateThreads, VPT == 1 ? 4 : 6) update_kernel(const UpdateArgs a) {
   constexpr int kECap = chunk_rollouts<BF16, M, VPT, kUpdateThreads>();
   __shared__ UpdateShared<kUpdateThreads, kECap, SRC == 1> sh;
   MJ_CHECK(blockDim.x == kUpdateThreads && (int)gridDim.x == a.chunks && (int)gridDim.y == a.groups &&
