@@ -215,10 +215,13 @@ mppi_status mppi_jump_step_async(mppi_jump_ctx* ctx, const float* x0, int32_t it
 
 /* Rollout launch shape ("tile").  rollout_variant 1 = fused: one kernel,
  * one thread per rollout, draws the noise and rolls out; 2 = split: a noise
- * pass over K x T/4 threads stores delta_eff and the jump counts, then one
- * thread per rollout runs the sequential dynamics (more parallelism when K
- * alone does not fill the GPU); 3 = staged: the split form with the step
- * data of each block's rollouts moved into shared memory by bulk copies;
+ * pass over K x T/4 threads stores delta_eff and the state-jump records
+ * (every step's while the rollout blocks of 128 fit on the SMs at once;
+ * beyond that jump masks, and a marks pass writes the records of the jumping
+ * steps), then one thread per rollout runs the sequential dynamics (more
+ * parallelism when K alone does not fill the GPU); 3 = staged: the split
+ * form with the step data of each block's rollouts moved into shared memory
+ * by bulk copies;
  * 4 = staged, and each rollout block also reduces its own rollouts to the
  * partial record of mppi_jump_rollout_partial (re-reading its perturbation
  * rows through shared memory), so that the update only combines the blocks'
