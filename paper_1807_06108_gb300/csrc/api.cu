@@ -46,6 +46,7 @@ IterBuffers ctx_buffers(mppi_jump_ctx* ctx, float* costs, int set) {
   b.costs = costs;
   b.dbg_counts = ctx->dbg_counts;
   b.dbg_J = ctx->dbg_J;
+  b.arm_key = nullptr;
   return b;
 }
 

@@ -97,6 +97,7 @@ struct IterBuffers {
   float* costs;        // may be NULL
   uint8_t* dbg_counts; // may be NULL
   float* dbg_J;        // may be NULL
+  uint32_t* arm_key;   // NULL, or a running minimum the noise pass re-arms (empty)
 };
 
 // Split variant, part 1: noise of iteration *it + it_off into b.noise etc.

@@ -257,7 +257,7 @@ static void launch_noise_t(const DevProblem& P, const IterBuffers& b, uint32_t i
   const bool sj = P.jump_channel == MPPI_JUMP_STATE;
   noise_kernel<M, BF16, DBG, MARKS><<<grid, kNoiseThreads, 0, s>>>(
       P, b.it, it_off, b.noise, sparse_mask(P, b), sj ? b.jrec : nullptr, marks_in_noise(P) ? 1 : 0,
-      b.dbg_counts, b.dbg_J, b.status);
+      b.dbg_counts, b.dbg_J, b.status, b.arm_key);
 }
 
 template <int M, bool BF16>

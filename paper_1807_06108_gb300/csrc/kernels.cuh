@@ -370,15 +370,18 @@ __device__ __forceinline__ void fused_rollout_thread(
 // then writes the records where a bit is set, and a record is read only
 // there, so none is ever cleared.  The pass touches nothing the rollout or
 // update of another iteration reads, so it can run concurrently with them on
-// a second buffer set.
+// a second buffer set.  arm_key (may be NULL): the running minimum to re-arm.
 // ---------------------------------------------------------------------------
 template <int M, bool BF16, bool DBG, bool MARKS>
 __global__ void __launch_bounds__(kNoiseThreads)
 noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t it_off,
              void* __restrict__ noise, uint32_t* __restrict__ jmask, float4* __restrict__ jrec,
              int jrec_marks, uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J,
-             int* __restrict__ status) {
+             int* __restrict__ status, uint32_t* __restrict__ arm_key) {
   static_assert(MARKS || !DBG, "the debug copy of J needs the marks");
+  // the first noise pass of an MPC step re-arms the running minimum of the
+  // step's first rollout (which launches after this pass)
+  if (arm_key && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *arm_key = kKeyEmpty;
   MJ_CHECK(blockDim.x == kNoiseThreads && 4 * (int)blockIdx.y < P.T && P.Kpad % 32 == 0 && P.K <= P.Kpad &&
                P.m == M,
            status);
