@@ -221,3 +221,46 @@ def test_autotune_keeps_results(cuda):
         np.testing.assert_array_equal(U_ref, s.controls())
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("tile", [None, (1, 128, 4), (2, 64, 4)], ids=["staged", "fused", "split"])
+def test_step_status_word_reports_and_clears(cuda, tile):
+    """A step whose every cost is non-finite (a NaN state) reports
+    MPPI_ENONFINITE and leaves U unchanged; reading the status word clears
+    it, so the next step from a finite state succeeds and is bit-equal to a
+    fresh context's step at the same counter (the step graph re-arms the
+    running minimum of its first iteration itself).  Both the synchronous
+    step and the asynchronous step followed by a sync."""
+    from paper_1807_06108_gb300 import mppi
+    prob = W.quadrotor_k4096(K=512, T=20, iters=3)
+    bad = np.full(12, np.nan, dtype=np.float32)
+    good = W.initial_state(prob)
+    s, ref = _solver(prob, tile), _solver(prob, tile)
+    try:
+        U0 = s.controls()
+        with pytest.raises(mppi.MppiError) as e:
+            s.step(bad)
+        assert e.value.code == mppi.ENONFINITE
+        np.testing.assert_array_equal(s.controls(), U0)
+        assert s.iteration() == prob["iters"]
+        u_s = s.step(good)
+        ref.set_iteration(prob["iters"])
+        u_ref = ref.step(good)
+        np.testing.assert_array_equal(u_s, u_ref)
+        np.testing.assert_array_equal(s.controls(), ref.controls())
+        # asynchronous: the error is reported by the next sync, then cleared
+        s.set_x0(bad)
+        mppi.mppi_jump_step_async(s.ctx, s.x0.data_ptr(), prob["iters"])
+        with pytest.raises(mppi.MppiError) as e:
+            s.sync()
+        assert e.value.code == mppi.ENONFINITE
+        s.set_x0(good)
+        mppi.mppi_jump_step_async(s.ctx, s.x0.data_ptr(), prob["iters"])
+        s.sync()
+        ref.set_x0(good)
+        mppi.mppi_jump_step_async(ref.ctx, ref.x0.data_ptr(), prob["iters"])
+        ref.sync()
+        assert s.iteration() == 4 * prob["iters"] and ref.iteration() == 3 * prob["iters"]
+    finally:
+        s.close()
+        ref.close()
