@@ -231,8 +231,9 @@ mppi_status mppi_jump_step_async(mppi_jump_ctx* ctx, const float* x0, int32_t it
  * run (2, 4 or 8); for the staged forms, steps per shared-memory stage (4, 8
  * or 16); for the fused form, steps per unrolled chunk (4, 8 or 16).  The
  * staged forms launch one extra (producer) warp per block.  The default is
- * staged, block 128, with 16-step stages while the rollout blocks fit on the
- * SMs about once and 8-step stages from two waves of blocks on.  Every tile
+ * staged with 16-step stages, block 96 while blocks of 96 fit on the SMs at
+ * once, else block 128, with 8-step stages from two waves of blocks of 128
+ * on.  Every tile
  * computes identical costs; tiles 1-3 give identical updates, tile 4 the
  * same update up to the summation order.  Setting a tile drops the cached
  * graphs. */

@@ -208,8 +208,13 @@ UpdateGeom update_geometry(int Kpad, int T, int m, bool bf16, int num_sms) {
 // Measured on GB300: the staged form (a producer warp moves the step data
 // into shared memory with bulk copies) is the fastest rollout at every size;
 // while the rollout blocks fit on the SMs about once, 16-step stages (one
-// block per SM, see launch_staged_t), beyond that 8-step stages so that
-// several blocks share an SM.
+// block per SM, see launch_staged), beyond that 8-step stages so that
+// several blocks share an SM.  While blocks of 96 fit on the SMs at once,
+// blocks of 96: three compute warps and the producer warp put one warp on
+// each scheduler, where with 128 one compute warp shares its scheduler with
+// the producer and holds the block back (quadrotor K = 4096: 0.2181 against
+// 0.2225 ms per MPC step, three runs each; cart-pole K = 1000: 0.0303
+// against 0.0306 ms).
 RolloutTile default_tile(const DevProblem& P, int num_sms) {
   const int sms = num_sms > 0 ? num_sms : 152;
   const int blocks = (P.Kpad + 127) / 128;
@@ -217,6 +222,7 @@ RolloutTile default_tile(const DevProblem& P, int num_sms) {
   t.variant = 3;
   t.block = 128;
   t.chunk = blocks >= 2 * sms ? 8 : 16;
+  if ((P.Kpad + 95) / 96 <= sms) t.block = 96;
   return t;
 }
 

@@ -75,7 +75,7 @@ def test_invalid_tile_rejected(cuda):
                     (1, 16, 4), (2, 64, 3)]:
             with pytest.raises(mppi.MppiError):
                 mppi.mppi_jump_set_tuning(s.ctx, *bad)
-        assert mppi.mppi_jump_get_tuning(s.ctx) == (3, 128, 16)
+        assert mppi.mppi_jump_get_tuning(s.ctx) == (3, 96, 16)
     finally:
         s.close()
 
