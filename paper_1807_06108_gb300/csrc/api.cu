@@ -250,6 +250,7 @@ mppi_status mppi_jump_init(const mppi_jump_config* cfg, void* stream, mppi_jump_
       ctx->own_stream = e == cudaSuccess;
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->arena, L.total);
     if (e == cudaSuccess) {
       char* a = (char*)ctx->arena;
@@ -312,6 +313,7 @@ mppi_status mppi_jump_destroy(mppi_jump_ctx* ctx) {
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->h_x0) cudaFreeHost(ctx->h_x0);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
+  if (ctx->aux2) cudaStreamDestroy(ctx->aux2);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return MPPI_OK;

@@ -15,6 +15,7 @@ struct mppi_jump_ctx {
   mj::RolloutTile tile;
   cudaStream_t stream = nullptr;  // every call enqueues here
   cudaStream_t aux = nullptr;     // second branch of the captured step (noise prefetch)
+  cudaStream_t aux2 = nullptr;    // third branch (marks passes of sparse jump records)
   bool own_stream = false;
   int device = 0;
   // one device allocation carved into the buffers below

@@ -101,7 +101,14 @@ struct IterBuffers {
 };
 
 // Split variant, part 1: noise of iteration *it + it_off into b.noise etc.
-cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s);
+// With s_marks (and ev) the marks pass of sparse jump records, when the
+// problem has one, runs on s_marks after an event hop, at the highest
+// priority; without, everything runs on s.
+cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s,
+                         cudaStream_t s_marks = nullptr, cudaEvent_t ev = nullptr);
+// Whether the problem's noise pass is followed by marks_kernel (sparse
+// state-jump records).
+bool has_marks_pass(const DevProblem& P);
 
 // State-channel jump records: dense (the noise pass draws the marks and
 // writes every step's record) while the rollout blocks of 128 fit on the SMs

@@ -257,11 +257,21 @@ uint32_t* sparse_mask(const DevProblem& P, const IterBuffers& b) {
   return P.jump_channel == MPPI_JUMP_STATE && !marks_in_noise(P) ? b.jmask : nullptr;
 }
 
+bool has_marks_pass(const DevProblem& P) {
+  return P.jump_channel == MPPI_JUMP_STATE && P.nmax > 0 && !marks_in_noise(P);
+}
+
 template <int M, bool BF16, bool DBG, bool MARKS>
 static void launch_noise_t(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s) {
-  const dim3 grid((P.Kpad + kNoiseThreads - 1) / kNoiseThreads, (P.T + 3) / 4);
+  // With sparse records the pass runs beside the rollout and update of the
+  // previous iteration; a block of 256 threads frees, when it retires, room
+  // for a rollout block (160 threads, 48 registers each), so the
+  // higher-priority rollout is not held off the SMs by noise blocks that
+  // keep refilling smaller gaps.
+  const int nt = has_marks_pass(P) ? kNoiseThreadsLarge : kNoiseThreads;
+  const dim3 grid((P.Kpad + nt - 1) / nt, (P.T + 3) / 4);
   const bool sj = P.jump_channel == MPPI_JUMP_STATE;
-  noise_kernel<M, BF16, DBG, MARKS><<<grid, kNoiseThreads, 0, s>>>(
+  noise_kernel<M, BF16, DBG, MARKS><<<grid, nt, 0, s>>>(
       P, b.it, it_off, b.noise, sparse_mask(P, b), sj ? b.jrec : nullptr, marks_in_noise(P) ? 1 : 0,
       b.dbg_counts, b.dbg_J, b.status, b.arm_key);
 }
@@ -278,7 +288,8 @@ static void launch_noise_m(const DevProblem& P, const IterBuffers& b, uint32_t i
   else launch_noise_t<M, BF16, false, false>(P, b, it_off, s);
 }
 
-cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s) {
+cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s,
+                         cudaStream_t s_marks, cudaEvent_t ev) {
   const bool dbg = b.dbg_counts != nullptr || b.dbg_J != nullptr;
   switch ((P.m == 4 ? 2 : 0) + (P.noise_bf16 ? 1 : 0)) {
     case 0: launch_noise_m<1, false>(P, b, it_off, dbg, s); break;
@@ -287,10 +298,18 @@ cudaError_t launch_noise(const DevProblem& P, const IterBuffers& b, uint32_t it_
     default: launch_noise_m<4, true>(P, b, it_off, dbg, s); break;
   }
   // state-channel jumps of large problems: their marks into the jump records
-  if (P.jump_channel == MPPI_JUMP_STATE && P.nmax > 0 && !marks_in_noise(P)) {
+  if (has_marks_pass(P)) {
     const int rows = P.Kpad / 32;
     const dim3 grid((rows + kMarkWarps - 1) / kMarkWarps, (P.T + 31) / 32);
-    marks_kernel<<<grid, kMarkThreads, 0, s>>>(P, b.it, it_off, b.jmask, b.jrec, b.status);
+    if (s_marks) {
+      cudaError_t e = cudaEventRecord(ev, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s_marks, ev, 0);
+      if (e != cudaSuccess) return e;
+      launch_hi(marks_kernel, grid, dim3(kMarkThreads), 0, s_marks, false, P, (const uint32_t*)b.it, it_off,
+                (const uint32_t*)b.jmask, b.jrec, b.status);
+    } else {
+      marks_kernel<<<grid, kMarkThreads, 0, s>>>(P, b.it, it_off, b.jmask, b.jrec, b.status);
+    }
   }
   return cudaGetLastError();
 }

@@ -18,7 +18,8 @@
 namespace mj {
 
 constexpr int kRolloutThreads = 128;
-constexpr int kNoiseThreads = 128;
+constexpr int kNoiseThreads = 128;       // noise-pass block, small problems
+constexpr int kNoiseThreadsLarge = 256;  // and with sparse jump records
 constexpr int kUpdateThreads = 256;
 constexpr int kStatusNonFinite = 5;
 constexpr int kStatusBounds = 7;  // MPPI_EBOUNDS
@@ -373,7 +374,7 @@ __device__ __forceinline__ void fused_rollout_thread(
 // a second buffer set.  arm_key (may be NULL): the running minimum to re-arm.
 // ---------------------------------------------------------------------------
 template <int M, bool BF16, bool DBG, bool MARKS>
-__global__ void __launch_bounds__(kNoiseThreads)
+__global__ void __launch_bounds__(kNoiseThreadsLarge)
 noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t it_off,
              void* __restrict__ noise, uint32_t* __restrict__ jmask, float4* __restrict__ jrec,
              int jrec_marks, uint8_t* __restrict__ dbg_counts, float* __restrict__ dbg_J,
@@ -382,10 +383,10 @@ noise_kernel(const DevProblem P, const uint32_t* __restrict__ it_ptr, uint32_t i
   // the first noise pass of an MPC step re-arms the running minimum of the
   // step's first rollout (which launches after this pass)
   if (arm_key && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *arm_key = kKeyEmpty;
-  MJ_CHECK(blockDim.x == kNoiseThreads && 4 * (int)blockIdx.y < P.T && P.Kpad % 32 == 0 && P.K <= P.Kpad &&
+  MJ_CHECK((blockDim.x == kNoiseThreads || blockDim.x == kNoiseThreadsLarge) && 4 * (int)blockIdx.y < P.T && P.Kpad % 32 == 0 && P.K <= P.Kpad &&
                P.m == M,
            status);
-  const int k = blockIdx.x * kNoiseThreads + threadIdx.x, b = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
   if (k >= P.Kpad) return;
   const bool active = k < P.K;
   const uint32_t it = __ldg(it_ptr) + it_off;
