@@ -264,10 +264,13 @@ bool has_marks_pass(const DevProblem& P) {
 template <int M, bool BF16, bool DBG, bool MARKS>
 static void launch_noise_t(const DevProblem& P, const IterBuffers& b, uint32_t it_off, cudaStream_t s) {
   // With sparse records the pass runs beside the rollout and update of the
-  // previous iteration; a block of 256 threads frees, when it retires, room
-  // for a rollout block (160 threads, 48 registers each), so the
-  // higher-priority rollout is not held off the SMs by noise blocks that
-  // keep refilling smaller gaps.
+  // previous iteration, in blocks of 256 threads: one retiring block leaves
+  // room for a rollout block (160 threads, 48 registers each).  Measured on
+  // GB300, large quadrotor, marks passes on their own branch: 0.935 ms per
+  // MPC step with 256-thread blocks, 0.949 with 512; 128-thread blocks gave
+  // 0.933 in a build that also had a third buffer set (each against about
+  // 0.964 for the build before, on its own box), so the size is not what
+  // decides the time.
   const int nt = has_marks_pass(P) ? kNoiseThreadsLarge : kNoiseThreads;
   const dim3 grid((P.Kpad + nt - 1) / nt, (P.T + 3) / 4);
   const bool sj = P.jump_channel == MPPI_JUMP_STATE;
