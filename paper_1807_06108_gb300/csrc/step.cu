@@ -66,8 +66,9 @@ mppi_status capture_step(mppi_jump_ctx* ctx, int iters, cudaGraphExec_t* exec) {
   // highest priority, so that the next noise pass starts on the second
   // branch as soon as the current one ends and fills the SMs beside it.
   // Measured on GB300, large quadrotor, with the per-node priorities below
-  // (one box): 0.9506 ms per MPC step with the marks passes on the noise
-  // branch, 0.9327 with them here.
+  // (one box, both builds with a third noise buffer set, which the library
+  // does not keep): 0.9487 ms per MPC step with the marks passes on the
+  // noise branch, 0.9327 with them here.
   cudaStream_t marks = has_marks_pass(ctx->P) ? ctx->aux2 : nullptr;
 
   cudaGraph_t graph = nullptr;
